@@ -1,0 +1,252 @@
+"""FP64 CPU oracle of the D3Q27 KBC step (arXiv:1507.02518).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()`` and by the
+CPU-baseline leg of ``bench.py``. The product package never imports it, and the two share no
+code. The arithmetic lives in ``kbc_oracle.c`` (plain C, FP64, compiled with
+``-O2 -ffp-contract=off``); this module only builds it and marshals numpy arrays.
+
+Field layout: ``f[27, nz, ny, nx]`` (plane i contiguous, x fastest), velocity index
+``i = (vx+1) + 3(vy+1) + 9(vz+1)``; macroscopic ``rho[nz, ny, nx]``, ``u[3, nz, ny, nx]``.
+
+Parity pins: every function here is pinned by ``tests/test_oracle_*.py`` against properties the
+paper and the mathematics fix (conservation, fixed point, LBGK/RLB limits, the moment-basis
+inverse, cube symmetry, entropy maximum, analytic decay rates, closed-form diagnostics). The
+exact-stabilizer root (``gamma_exact``) is pinned only through the entropy-maximum property and
+its limit toward eq:result21.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "kbc_oracle.c")
+_HDR = os.path.join(_HERE, "kbc_oracle.h")
+_LIB = os.path.join(_HERE, "liborc.so")
+_lock = threading.Lock()
+_lib = None
+
+S_D, S_DT, S_DQ, S_DTQ = 0, 1, 2, 3
+GAMMA_ESTIMATE, GAMMA_LBGK, GAMMA_RLB, GAMMA_EXACT = 0, 1, 2, 3
+DEN_GUARD = 1e-300
+
+
+def build(force: bool = False) -> str:
+    """Compile ``liborc.so`` with gcc (OpenMP if available). Returns the library path."""
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
+        return _LIB
+    base = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-fPIC", "-shared"]
+    tmp = _LIB + ".tmp%d" % os.getpid()
+    try:
+        subprocess.run(base + ["-fopenmp", _SRC, "-o", tmp, "-lm"], check=True,
+                       capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base + [_SRC, "-o", tmp, "-lm"], check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB)
+            d, i32, i64, vp = ctypes.c_double, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+            L.orc_beta.restype = d
+            L.orc_beta.argtypes = [d]
+            L.orc_lattice.argtypes = [vp, vp]
+            L.orc_equilibrium.argtypes = [d, vp, vp]
+            L.orc_moments.argtypes = [vp, vp, vp]
+            L.orc_table1.argtypes = [vp, d, vp, vp, vp, vp]
+            L.orc_moment_rep.argtypes = [vp, d, vp]
+            L.orc_collide.restype = ctypes.c_int
+            L.orc_collide.argtypes = [vp, d, ctypes.c_int, ctypes.c_int, vp, vp]
+            L.orc_collide_mirror.argtypes = [vp, d, ctypes.c_int, d, vp]
+            L.orc_deltas.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+            L.orc_gamma_exact.restype = d
+            L.orc_gamma_exact.argtypes = [vp, vp, vp, d, d]
+            L.orc_entropy.restype = d
+            L.orc_entropy.argtypes = [vp]
+            L.orc_stream.argtypes = [i32, i32, i32, vp, vp]
+            L.orc_collide_field.restype = i64
+            L.orc_collide_field.argtypes = [i32, i32, i32, vp, d, ctypes.c_int, ctypes.c_int, vp]
+            L.orc_init_equilibrium.argtypes = [i32, i32, i32, vp, vp, vp]
+            L.orc_macroscopic.argtypes = [i32, i32, i32, vp, vp, vp]
+            L.orc_diagnostics.argtypes = [i32, i32, i32, vp, vp, d, vp]
+            L.orc_run.restype = i64
+            L.orc_run.argtypes = [i32, i32, i32, vp, vp, i64, d, ctypes.c_int, ctypes.c_int,
+                                       vp]
+            L.orc_num_threads.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _null():
+    return ctypes.c_void_p(0)
+
+
+# ---------------------------------------------------------------- single node
+
+def lattice():
+    """(v[27,3] int, W[27]) in the order i = (vx+1) + 3(vy+1) + 9(vz+1)."""
+    v = np.zeros((27, 3), dtype=np.int32)
+    w = np.zeros(27)
+    lib().orc_lattice(v.ctypes.data_as(ctypes.c_void_p), _p(w))
+    return v.astype(np.int64), w
+
+
+def beta(nu: float) -> float:
+    return lib().orc_beta(nu)
+
+
+def equilibrium(rho: float, u) -> np.ndarray:
+    u = _f64(u)
+    out = np.zeros(27)
+    lib().orc_equilibrium(float(rho), _p(u), _p(out))
+    return out
+
+
+def moments(f):
+    """(rho, M[3,3,3]) with M[p,q,r] = sum f v^p v^q v^r / rho (eq:natmoments)."""
+    f = _f64(f)
+    rho = np.zeros(1)
+    M = np.zeros(27)
+    lib().orc_moments(_p(f), _p(rho), _p(M))
+    return float(rho[0]), M.reshape(3, 3, 3)
+
+
+def table1(M, rho):
+    """(k, d, t, q) parts of Table 1 for unit-density moments M[3,3,3]."""
+    M = _f64(M).reshape(27)
+    k, d, t, q = (np.zeros(27) for _ in range(4))
+    lib().orc_table1(_p(M), float(rho), _p(k), _p(d), _p(t), _p(q))
+    return k, d, t, q
+
+
+def moment_rep(M, rho):
+    M = _f64(M).reshape(27)
+    f = np.zeros(27)
+    lib().orc_moment_rep(_p(M), float(rho), _p(f))
+    return f
+
+
+def collide(f, beta_, variant=S_DTQ, gamma_mode=GAMMA_ESTIMATE):
+    """One KBC collision of a single node. Returns (f', gamma, guarded)."""
+    f = _f64(f)
+    out = np.zeros(27)
+    g = np.zeros(1)
+    guarded = lib().orc_collide(_p(f), float(beta_), int(variant), int(gamma_mode), _p(out),
+                                _p(g))
+    return out, float(g[0]), bool(guarded)
+
+
+def collide_mirror(f, beta_, variant, gamma):
+    f = _f64(f)
+    out = np.zeros(27)
+    lib().orc_collide_mirror(_p(f), float(beta_), int(variant), float(gamma), _p(out))
+    return out
+
+
+def deltas(f, variant=S_DTQ):
+    """(f_eq, ds, dh) of the collision listing, steps 2-5."""
+    f = _f64(f)
+    feq, ds, dh = np.zeros(27), np.zeros(27), np.zeros(27)
+    lib().orc_deltas(_p(f), int(variant), _p(feq), _p(ds), _p(dh))
+    return feq, ds, dh
+
+
+def gamma_exact(feq, ds, dh, beta_, gamma0):
+    feq, ds, dh = _f64(feq), _f64(ds), _f64(dh)
+    return lib().orc_gamma_exact(_p(feq), _p(ds), _p(dh), float(beta_), float(gamma0))
+
+
+def entropy(f) -> float:
+    f = _f64(f)
+    return lib().orc_entropy(_p(f))
+
+
+# ---------------------------------------------------------------- fields
+
+def _shape(f):
+    assert f.ndim == 4 and f.shape[0] == 27
+    nz, ny, nx = f.shape[1:]
+    return int(nx), int(ny), int(nz)
+
+
+def stream(f) -> np.ndarray:
+    """Periodic propagation g_i(x) = f_i(x - v_i)."""
+    f = _f64(f)
+    nx, ny, nz = _shape(f)
+    out = np.empty_like(f)
+    lib().orc_stream(nx, ny, nz, _p(f), _p(out))
+    return out
+
+
+def collide_field(f, beta_, variant=S_DTQ, gamma_mode=GAMMA_ESTIMATE, want_gamma=False):
+    """Collide every node. Returns (f', gamma_field or None, guarded_count)."""
+    f = _f64(f).copy()
+    nx, ny, nz = _shape(f)
+    g = np.zeros((nz, ny, nx)) if want_gamma else None
+    guarded = lib().orc_collide_field(nx, ny, nz, _p(f), float(beta_), int(variant),
+                                      int(gamma_mode), _p(g) if want_gamma else _null())
+    return f, g, int(guarded)
+
+
+def init_equilibrium(rho, u) -> np.ndarray:
+    rho, u = _f64(rho), _f64(u)
+    nz, ny, nx = rho.shape
+    f = np.empty((27, nz, ny, nx))
+    lib().orc_init_equilibrium(nx, ny, nz, _p(rho), _p(u), _p(f))
+    return f
+
+
+def macroscopic(f):
+    f = _f64(f)
+    nx, ny, nz = _shape(f)
+    rho = np.empty((nz, ny, nx))
+    u = np.empty((3, nz, ny, nx))
+    lib().orc_macroscopic(nx, ny, nz, _p(f), _p(rho), _p(u))
+    return rho, u
+
+
+def diagnostics(rho, u, nu):
+    """dict(mass, momentum[3], kinetic_energy, enstrophy, dissipation) from rho, u."""
+    rho, u = _f64(rho), _f64(u)
+    nz, ny, nx = rho.shape
+    out = np.zeros(8)
+    lib().orc_diagnostics(nx, ny, nz, _p(rho), _p(u), float(nu), _p(out))
+    return {"mass": out[0], "momentum": out[1:4].copy(), "kinetic_energy": out[4],
+            "enstrophy": out[5], "dissipation": out[6]}
+
+
+def run(f, nsteps, beta_, variant=S_DTQ, gamma_mode=GAMMA_ESTIMATE, want_gamma=False):
+    """nsteps of collide-then-stream from the pre-collision field f(t).
+
+    Returns (f(t + nsteps), gamma of the last collision or None, guarded count).
+    """
+    fa = _f64(f).copy()
+    nx, ny, nz = _shape(fa)
+    fb = np.empty_like(fa)
+    g = np.zeros((nz, ny, nx)) if want_gamma else None
+    guarded = lib().orc_run(nx, ny, nz, _p(fa), _p(fb), int(nsteps), float(beta_),
+                            int(variant), int(gamma_mode), _p(g) if want_gamma else _null())
+    return fa, g, int(guarded)
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())

@@ -1,0 +1,120 @@
+"""Seeded synthetic inputs (initial density and velocity fields) for the KBC step.
+
+This module holds input generation only: no lattice-Boltzmann arithmetic (no equilibrium,
+moments or collision). Both the CUDA path and the CPU oracle take their inputs from here.
+
+Arrays are float64, indexed ``[z, y, x]`` (x fastest); velocities are ``u[3, z, y, x]``.
+Node ``j`` on an axis of ``n`` nodes sits at ``x_j = 2*pi*j/n`` when a flow is written on
+``[0, 2*pi]`` (Sec. "Numerical Simulations", eq:kida).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+BATCH_EDGES = (32, 48, 64, 96, 128)
+BATCH_BASE_SEED = 20150702
+
+
+def _grid(nx: int, ny: int, nz: int):
+    z, y, x = np.meshgrid(np.arange(nz, dtype=np.float64), np.arange(ny, dtype=np.float64),
+                          np.arange(nx, dtype=np.float64), indexing="ij")
+    return x, y, z
+
+
+def taylor_green(n: int, u0: float = 0.05, k: float | None = None):
+    """3D Taylor-Green vortex: u = u0 sin kx cos ky cos kz, v = -u0 cos kx sin ky cos kz, w = 0.
+
+    ``k`` defaults to 2*pi/n (one period per box). Density is 1.
+    """
+    k = 2.0 * math.pi / n if k is None else k
+    x, y, z = _grid(n, n, n)
+    u = np.zeros((3, n, n, n))
+    u[0] = u0 * np.sin(k * x) * np.cos(k * y) * np.cos(k * z)
+    u[1] = -u0 * np.cos(k * x) * np.sin(k * y) * np.cos(k * z)
+    return np.ones((n, n, n)), u
+
+
+def taylor_green_2d(n: int, nz: int, u0: float):
+    """z-invariant 2D Taylor-Green vortex on an n x n x nz box (density 1)."""
+    k = 2.0 * math.pi / n
+    x, y, _ = _grid(n, n, nz)
+    u = np.zeros((3, nz, n, n))
+    u[0] = u0 * np.sin(k * x) * np.cos(k * y)
+    u[1] = -u0 * np.cos(k * x) * np.sin(k * y)
+    return np.ones((nz, n, n)), u
+
+
+def shear_wave(nx: int, ny: int, nz: int, u0: float, mode: int = 1):
+    """Transverse shear wave u_x = u0 sin(2 pi mode y / ny) (density 1)."""
+    x, y, _ = _grid(nx, ny, nz)
+    u = np.zeros((3, nz, ny, nx))
+    u[0] = u0 * np.sin(2.0 * math.pi * mode * y / ny)
+    return np.ones((nz, ny, nx)), u
+
+
+def kida(n: int, U0: float = 0.05):
+    """Kida vortex (eq:kida) on x, y, z in [0, 2 pi) sampled at 2 pi j / n; density 1."""
+    h = 2.0 * math.pi / n
+    x, y, z = (a * h for a in _grid(n, n, n))
+    u = np.zeros((3, n, n, n))
+    u[0] = U0 * np.sin(x) * (np.cos(3 * y) * np.cos(z) - np.cos(y) * np.cos(3 * z))
+    u[1] = U0 * np.sin(y) * (np.cos(3 * z) * np.cos(x) - np.cos(z) * np.cos(3 * x))
+    u[2] = U0 * np.sin(z) * (np.cos(3 * x) * np.cos(y) - np.cos(x) * np.cos(3 * y))
+    return np.ones((n, n, n)), u
+
+
+def random_spectrum(n: int, k0: float, urms: float, seed: int, dtype=np.float64):
+    """Random-phase solenoidal field with shell spectrum E(k) ~ k^4 exp(-2 (k/k0)^2).
+
+    ``k0`` is the peak wavenumber in units of 2 pi / n. White Gaussian noise per component
+    is transformed, shaped so that each spherical shell carries energy proportional to
+    E(k), projected onto divergence-free modes, stripped of the mean and Nyquist modes, and
+    transformed back; the result is scaled so that the r.m.s. of one component,
+    ``sqrt(<u.u>/3)``, equals ``urms`` (the u' of Table 2's caption). Density is 1.
+    """
+    rng = np.random.default_rng(seed)
+    kf = np.fft.fftfreq(n) * n
+    kr = np.fft.rfftfreq(n) * n
+    KZ, KY, KX = np.meshgrid(kf, kf, kr, indexing="ij")
+    K2 = KX * KX + KY * KY + KZ * KZ
+    K = np.sqrt(K2)
+    # |a|^2 per mode ~ E(K) / K^2 so that a shell (4 pi K^2 modes) carries E(K)
+    amp = K * np.exp(-((K / k0) ** 2))
+    nyq = n // 2
+    mask = (np.abs(KX) == nyq) | (np.abs(KY) == nyq) | (np.abs(KZ) == nyq) | (K == 0)
+    amp[mask] = 0.0
+    a = np.empty((3,) + K.shape, dtype=np.complex128)
+    for c in range(3):
+        a[c] = np.fft.rfftn(rng.standard_normal((n, n, n))) * amp
+    with np.errstate(divide="ignore", invalid="ignore"):
+        kdota = (KX * a[0] + KY * a[1] + KZ * a[2]) / np.where(K2 > 0, K2, 1.0)
+    a[0] -= KX * kdota
+    a[1] -= KY * kdota
+    a[2] -= KZ * kdota
+    u = np.stack([np.fft.irfftn(a[c], s=(n, n, n)) for c in range(3)])
+    rms = math.sqrt(float(np.mean(np.sum(u * u, axis=0))) / 3.0)
+    u *= urms / rms
+    return np.ones((n, n, n)), u.astype(dtype, copy=False)
+
+
+def population_noise(nx: int, ny: int, nz: int, seed: int):
+    """Uniform noise in [-1, 1] shaped like a population field, [27, z, y, x]."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-1.0, 1.0, size=(27, nz, ny, nx))
+
+
+def batch_boxes(nbox: int = 96, seed: int = BATCH_BASE_SEED):
+    """Parameters of the batched decaying-turbulence ensemble.
+
+    Edge uniform in {32, 48, 64, 96, 128}; k0 ~ U[2, 6]; u_rms ~ U[0.02, 0.06];
+    nu log-uniform in [1e-5, 1e-3]; the field of box b is seeded with ``seed + b``.
+    """
+    rng = np.random.default_rng(seed)
+    edges = rng.choice(np.array(BATCH_EDGES), size=nbox)
+    k0 = rng.uniform(2.0, 6.0, size=nbox)
+    urms = rng.uniform(0.02, 0.06, size=nbox)
+    nu = np.exp(rng.uniform(math.log(1e-5), math.log(1e-3), size=nbox))
+    return [{"n": int(edges[b]), "k0": float(k0[b]), "urms": float(urms[b]),
+             "nu": float(nu[b]), "seed": int(seed + b)} for b in range(nbox)]

@@ -1,0 +1,94 @@
+"""Physics pins of the oracle: decay rates the viscosity relation fixes, and closed-form
+diagnostics on the discrete grid (arXiv:1507.02518, eq:viscosity, Sec. "Numerical Simulations").
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1507_02518_gb300 import workloads as wl
+
+
+def shear_amplitude(f, ny):
+    rho, u = oracle.macroscopic(f)
+    y = np.arange(ny)
+    s = np.sin(2 * math.pi * y / ny)
+    return 2.0 / ny * float(np.mean(u[0], axis=(0, 2)) @ s)
+
+
+@pytest.mark.parametrize("variant,mode", [(oracle.S_DTQ, oracle.GAMMA_ESTIMATE),
+                                          (oracle.S_D, oracle.GAMMA_ESTIMATE),
+                                          (oracle.S_DT, oracle.GAMMA_ESTIMATE),
+                                          (oracle.S_DQ, oracle.GAMMA_ESTIMATE),
+                                          (oracle.S_DTQ, oracle.GAMMA_LBGK)])
+def test_shear_wave_decays_at_lattice_viscosity(variant, mode):
+    """u_x = U sin(k y) decays as exp(-nu k^2 t), nu = c_s^2 (1/(2 beta) - 1/2), for any gamma."""
+    nx, ny, nz = 3, 32, 3
+    nu = 0.02
+    b = oracle.beta(nu)
+    rho, u = wl.shear_wave(nx, ny, nz, 1e-4)
+    f = oracle.init_equilibrium(rho, u)
+    f, _, _ = oracle.run(f, 40, b, variant, mode)       # let the initial transient pass
+    a0 = shear_amplitude(f, ny)
+    steps = 400
+    f, _, _ = oracle.run(f, steps, b, variant, mode)
+    a1 = shear_amplitude(f, ny)
+    k = 2 * math.pi / ny
+    nu_fit = -math.log(a1 / a0) / (k * k * steps)
+    assert nu_fit == pytest.approx(nu, rel=0.02)
+
+
+def test_taylor_green_2d_energy_decay():
+    """z-invariant Taylor-Green: E ~ exp(-2 nu |k|^2 t) with |k|^2 = 2 (2 pi / n)^2."""
+    n, nz = 24, 3
+    nu = 0.02
+    b = oracle.beta(nu)
+    rho, u = wl.taylor_green_2d(n, nz, 1e-4)
+    f = oracle.init_equilibrium(rho, u)
+    f, _, _ = oracle.run(f, 20, b)
+
+    def energy(f):
+        _, uu = oracle.macroscopic(f)
+        return 0.5 * float(np.mean(np.sum(uu * uu, axis=0)))
+
+    e0 = energy(f)
+    steps = 200
+    f, _, _ = oracle.run(f, steps, b)
+    e1 = energy(f)
+    k2 = 2 * (2 * math.pi / n) ** 2
+    nu_fit = -math.log(e1 / e0) / (2 * k2 * steps)
+    assert nu_fit == pytest.approx(nu, rel=0.02)
+
+
+def test_kida_initial_kinetic_energy_closed_form():
+    """k(0) of eq:kida on the grid is exactly 3 U0^2 / 8 (trigonometric orthogonality)."""
+    U0 = 0.05
+    rho, u = wl.kida(16, U0)
+    d = oracle.diagnostics(rho, u, 1e-3)
+    assert d["kinetic_energy"] == pytest.approx(3 * U0 * U0 / 8, rel=1e-13)
+    assert d["mass"] == pytest.approx(16 ** 3, rel=1e-15)
+    assert np.allclose(d["momentum"], 0.0, atol=1e-13)
+
+
+def test_shear_wave_diagnostics_closed_form():
+    """2nd-order central differences of U sin(k y): Omega = U^2 sin^2 k / 4, eps = nu U^2 sin^2 k / 2."""
+    U, nu = 0.03, 2e-3
+    for ny, mode in ((16, 1), (16, 3), (20, 2)):
+        rho, u = wl.shear_wave(4, ny, 5, U, mode)
+        d = oracle.diagnostics(rho, u, nu)
+        kk = 2 * math.pi * mode / ny
+        assert d["kinetic_energy"] == pytest.approx(U * U / 4, rel=1e-13)
+        assert d["enstrophy"] == pytest.approx(U * U * math.sin(kk) ** 2 / 4, rel=1e-12)
+        assert d["dissipation"] == pytest.approx(nu * U * U * math.sin(kk) ** 2 / 2, rel=1e-12)
+
+
+def test_mean_flow_is_removed_from_statistics():
+    """u' = u - <u> (Sec. "Numerical Simulations"): a uniform offset changes neither k nor Omega."""
+    rho, u = wl.shear_wave(4, 16, 4, 0.02, 2)
+    d0 = oracle.diagnostics(rho, u, 1e-3)
+    u2 = u.copy()
+    u2[1] += 0.01
+    d1 = oracle.diagnostics(rho, u2, 1e-3)
+    for key in ("kinetic_energy", "enstrophy", "dissipation"):
+        assert d1[key] == pytest.approx(d0[key], rel=1e-12)
