@@ -1,0 +1,497 @@
+"""Benchmark of the D3Q27 KBC step on GB300: MLUPS and fraction of the HBM roofline.
+
+Default workload (one JSON line on rank 0): decaying homogeneous isotropic turbulence on a
+periodic 256^3 box (seeded random-phase solenoidal field, E(k) ~ k^4 exp(-2 (k/k0)^2), k0 = 4,
+u_rms = 0.04, rho0 = 1, nu = 2e-4), KBC s = d+t+q, FP32 storage of f - W with FP32 collision,
+pull streaming, kinetic-energy / enstrophy diagnostics every 50 steps. A "step" is one lattice
+update of the whole box. Other storage / scheme / batched variants are reported under
+"variants" in the same line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun) runs independent replicas, one per GPU (weak scaling, no data-path
+collective); value = all ranks' lattice updates / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import signal
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & % HBM roofline, D3Q27 KBC step; FP32/FP16/batched vs FP64 at stated err"
+FALLBACK_HBM_GBS = 6800.0
+BYTES_PER_LUP = {"f64": 432, "f32": 216, "f16": 108}   # read 27 + write 27 values
+MAIN = {"name": "hit256_f32_pull", "n": 256, "field": "spectrum", "k0": 4.0, "urms": 0.04,
+        "nu": 2e-4, "seed": 1, "storage": "f32", "scheme": "pull", "diag_every": 50}
+VARIANTS = [
+    {"name": "hit256_f64_pull", "n": 256, "field": "spectrum", "k0": 4.0, "urms": 0.04,
+     "nu": 2e-4, "seed": 1, "storage": "f64", "scheme": "pull", "diag_every": 50, "steps": 100},
+    {"name": "hit256_f32_aa", "n": 256, "field": "spectrum", "k0": 4.0, "urms": 0.04,
+     "nu": 2e-4, "seed": 1, "storage": "f32", "scheme": "aa", "diag_every": 50, "steps": 400},
+    {"name": "hit256_f16_aa", "n": 256, "field": "spectrum", "k0": 4.0, "urms": 0.04,
+     "nu": 2e-4, "seed": 1, "storage": "f16", "scheme": "aa", "diag_every": 50, "steps": 400},
+    {"name": "kida512_f32_aa", "n": 512, "field": "kida", "U0": 0.05, "nu": 5e-5,
+     "storage": "f32", "scheme": "aa", "diag_every": 50, "steps": 200},
+    {"name": "kida512_f16_aa", "n": 512, "field": "kida", "U0": 0.05, "nu": 5e-5,
+     "storage": "f16", "scheme": "aa", "diag_every": 50, "steps": 200},
+    {"name": "batch96_f32_pull", "field": "batch", "nbox": 96, "storage": "f32",
+     "scheme": "pull", "steps": 200},
+]
+# DRAM bytes per lattice update of the FP32 pull step kernel from an ncu capture, keyed by a
+# hash of the kernel sources; a changed kernel gets no traffic figure until re-profiled.
+NCU_TRAFFIC_PER_LUP = {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1507_02518_gb300", "csrc")
+    for name in ("kbc_device.cuh", "kbc_kernels.cuh", "kbc_f32.cu"):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        for key in ("hbm_gbs", "hbm_copy_gbs", "hbm_GBps"):
+            if key in d:
+                return float(d[key]), "measured"
+    except (OSError, ValueError):
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+# ---------------------------------------------------------------- distributed plumbing
+
+def dist_init(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("KBC_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % index)
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.send_signal(signal.SIGTERM)
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        except OSError:
+            pass
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- workloads
+
+def make_field(w):
+    from paper_1507_02518_gb300 import workloads
+    if w["field"] == "spectrum":
+        return workloads.random_spectrum(w["n"], w["k0"], w["urms"], w["seed"])
+    if w["field"] == "kida":
+        return workloads.kida(w["n"], w["U0"])
+    if w["field"] == "tgv":
+        return workloads.taylor_green(w["n"], w.get("u0", 0.05))
+    raise ValueError(w["field"])
+
+
+def run_box(w, steps, warmup, want_kernel_time=True):
+    """Time `steps` steps of one box (inputs resident in HBM). Returns a dict."""
+    import torch
+    from paper_1507_02518_gb300 import lb
+    rho, u = make_field(w)
+    lat = lb.Lattice(w["n"], nu=w["nu"], storage=w["storage"], scheme=w["scheme"])
+    st = lat.stream
+    lat.init_field(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
+    del rho, u
+    lat.step(warmup)
+    torch.cuda.synchronize()
+    every = w.get("diag_every", 0) or steps
+    chunks = []
+    k = 0
+    while k < steps:
+        c = min(every, steps - k)
+        chunks.append(c)
+        k += c
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in chunks]
+    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    diags = []
+    torch.cuda.synchronize()
+    e_start.record(st)
+    for (a, b), c in zip(ev, chunks):
+        a.record(st)
+        lat.step(c)
+        b.record(st)
+        if w.get("diag_every"):
+            diags.append(lat.diagnostics())
+    e_end.record(st)
+    torch.cuda.synchronize()
+    total_ms = e_start.elapsed_time(e_end)
+    step_ms = sum(a.elapsed_time(b) for a, b in ev)
+    launches = steps + (3 * len(diags))
+    out = {"P": lat.P, "steps": steps, "total_ms": total_ms, "step_kernel_ms": step_ms / steps,
+           "launches": launches, "diag": diags[-1] if diags else None, "lat": lat}
+    return out
+
+
+def run_batch(w, steps, warmup):
+    import torch
+    from paper_1507_02518_gb300 import lb, workloads
+    boxes = workloads.batch_boxes(w["nbox"])
+    batch = lb.Batch(boxes, storage=w["storage"], scheme=w["scheme"])
+    tune = batch.autotune(2)                      # on the rest state, before the fields
+    for k, b in enumerate(boxes):
+        rho, u = workloads.random_spectrum(b["n"], b["k0"], b["urms"], b["seed"])
+        lb.lb_init_field(batch.box(k), 0, np.ascontiguousarray(u).ctypes.data, False)
+    batch.step(warmup)
+    torch.cuda.synchronize()
+    st = batch.stream
+    a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    batch.step(steps)                             # capture the graph for this step count
+    torch.cuda.synchronize()
+    a.record(st)
+    batch.step(steps)                             # replay: one graph launch, `steps` kernels
+    b_.record(st)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b_)
+    diags = batch.diagnostics()
+    # the same boxes stepped one at a time (box-by-box launches, no graph)
+    single_ms = 0.0
+    lat_steps = max(1, steps // 10)
+    for k in range(len(boxes)):
+        view = batch.box(k)
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(st)
+        lb.lb_step(view, lat_steps)
+        s1.record(st)
+        torch.cuda.synchronize()
+        single_ms += s0.elapsed_time(s1)
+    return {"P": batch.nodes, "steps": steps, "total_ms": ms, "tune": tune,
+            "single_box_ms_per_step": single_ms / lat_steps, "diags": diags}
+
+
+def run_e2e(w, steps):
+    """Same metric through the public API with host buffers: H2D of the initial fields, the
+    steps with diagnostics, D2H of the final rho and u, all inside the timed region."""
+    import torch
+    from paper_1507_02518_gb300 import lb
+    rho, u = make_field(w)
+    rho = np.ascontiguousarray(rho)
+    u = np.ascontiguousarray(u)
+    lat = lb.Lattice(w["n"], nu=w["nu"], storage=w["storage"], scheme=w["scheme"])
+    rho_out = np.empty_like(rho)
+    u_out = np.empty_like(u)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lat.init_field(rho, u)
+    every = w.get("diag_every", 0) or steps
+    k = 0
+    while k < steps:
+        c = min(every, steps - k)
+        lat.step(c)
+        k += c
+        if w.get("diag_every"):
+            lat.diagnostics()
+    lb.lb_moments(lat.ctx, rho_out.ctypes.data, u_out.ctypes.data, False)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    h2d = rho.nbytes + u.nbytes
+    d2h = rho_out.nbytes + u_out.nbytes + (steps // every) * (16 * 8 + 8)
+    return {"value": lat.P * steps / dt / 1e6, "unit": "MLUPS",
+            "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps}
+
+
+def cpu_baseline(w, budget_s=12.0):
+    """The FP64 oracle (as it stands) on a bounded sample of the workload: a 64^3 box of the
+    same field family and parameters, stepped until about budget_s seconds of CPU work."""
+    import oracle
+    from paper_1507_02518_gb300 import workloads
+    n = 64
+    if w["field"] == "spectrum":
+        rho, u = workloads.random_spectrum(n, w["k0"], w["urms"], w["seed"])
+    elif w["field"] == "kida":
+        rho, u = workloads.kida(n, w["U0"])
+    else:
+        rho, u = workloads.taylor_green(n, 0.05)
+    f = oracle.init_equilibrium(rho, u)
+    beta = oracle.beta(w["nu"])
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        f, _, _ = oracle.run(f, 1, beta)
+        steps += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n ** 3 * steps / dt / 1e6, "unit": "MLUPS", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": "%d steps of a %d^3 box of the same field family (FP64 oracle, %.1f s)"
+                      % (steps, n, dt)}
+
+
+def roofline(storage, mlups, peak, peak_kind, traffic=None):
+    bpl = BYTES_PER_LUP[storage]
+    achieved = bpl * mlups * 1e6 / 1e9
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic,
+            "peak_source": "of %s" % peak_kind, "bytes_per_lup": bpl}
+
+
+# ---------------------------------------------------------------- arms
+
+def main_ours(args, rank, world, local):
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1507_02518_gb300 import lb
+    lb.load()
+    w = dict(MAIN)
+    peak, peak_kind = hbm_peak()
+    # warm-up and timed region (max over ranks)
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        res = run_box(w, args.steps, args.warmup)
+    barrier(world)
+    torch.cuda.synchronize()
+    ms_max = max_over_ranks(res["total_ms"], world)
+    total_lups = sum_over_ranks(float(res["P"] * args.steps), world)
+    value = total_lups / (ms_max / 1e3) / 1e6
+    kernel_ms = res["step_kernel_ms"]
+    kernel_mlups = res["P"] / (kernel_ms / 1e3) / 1e6
+    h = kernel_source_hash()
+    traffic = NCU_TRAFFIC_PER_LUP.get(h)
+    rl = roofline("f32", kernel_mlups, peak, peak_kind,
+                  None if traffic is None else traffic * res["P"])
+    rl["kernel"] = "kbc::step_kernel<float, MODE_PULL>"
+    rl["kernel_ms"] = round(kernel_ms, 5)
+    del res["lat"]
+    torch.cuda.empty_cache()
+
+    variants = {}
+    if not args.no_variants:
+        for v in VARIANTS:
+            try:
+                vs = v.get("steps", 200)
+                if v["field"] == "batch":
+                    r = run_batch(v, vs, 3)
+                    mlups = r["P"] * vs / (r["total_ms"] / 1e3) / 1e6
+                    single = r["P"] / (r["single_box_ms_per_step"] / 1e3) / 1e6
+                    variants[v["name"]] = {
+                        "MLUPS": round(mlups, 1), "nodes": r["P"], "steps": vs,
+                        "single_box_MLUPS": round(single, 1),
+                        "autotune": {"threads": r["tune"][0], "tile": r["tune"][1]},
+                        "frac_hbm": roofline(v["storage"], mlups, peak, peak_kind)["frac"],
+                        "finite": all(d["nonfinite_count"] == 0 for d in r["diags"])}
+                else:
+                    r = run_box(v, vs, 3)
+                    mlups = r["P"] * vs / (r["total_ms"] / 1e3) / 1e6
+                    kml = r["P"] / (r["step_kernel_ms"] / 1e3) / 1e6
+                    d = r["diag"]
+                    variants[v["name"]] = {
+                        "MLUPS": round(mlups, 1), "kernel_MLUPS": round(kml, 1), "steps": vs,
+                        "frac_hbm": roofline(v["storage"], kml, peak, peak_kind)["frac"],
+                        "kinetic_energy": d["kinetic_energy"], "gamma_mean": d["gamma_mean"]}
+                    del r["lat"]
+                torch.cuda.empty_cache()
+            except Exception as e:  # report, do not hide
+                variants[v["name"]] = {"error": str(e)[:200]}
+
+    e2e = run_e2e(w, args.steps) if not args.no_e2e else None
+    out = None
+    if rank == 0:
+        cpu = cpu_baseline(w) if (world == 1 and not args.no_cpu) else None
+        out = {
+            "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "hit256_f32_pull: periodic 256^3 decaying HIT, seeded random "
+                                   "solenoidal field E(k)~k^4 exp(-2(k/k0)^2), k0=4, u_rms=0.04, "
+                                   "rho0=1, nu=2e-4, KBC s=d+t+q, FP32 (f-W) storage + FP32 "
+                                   "collision, pull streaming, diagnostics every 50 steps",
+                       "box": [256, 256, 256], "storage": "f32", "scheme": "pull",
+                       "variant": "d+t+q", "diag_every": 50,
+                       "l2": "working set %.1f GB per step >> 129 MB L2 (no flush needed)"
+                             % (2 * 27 * 4 * res["P"] / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": rl, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": res["launches"],
+            "clocks": clk.summary(),
+            "diag_last": {k: res["diag"][k] for k in ("step", "kinetic_energy", "enstrophy",
+                                                      "dissipation", "gamma_mean", "gamma_std",
+                                                      "nonfinite_count")} if res["diag"] else None,
+            "variants": variants, "kernel_hash": h,
+        }
+        print(json.dumps(out), flush=True)
+    barrier(world)
+    return out
+
+
+def main_reference(args, rank, world):
+    """The reference arm: the FP64 CPU oracle, as it stands, on the machine's host cores."""
+    if rank != 0:
+        return None
+    w = dict(MAIN)
+    import oracle
+    from paper_1507_02518_gb300 import workloads
+    # each step is a bounded sample of the workload: an n^3 sub-box of the same field family,
+    # n chosen so that warm-up + timed steps stay around a minute of oracle time
+    n = int(round((40e6 / max(1, args.steps + args.warmup)) ** (1.0 / 3.0)))
+    n = max(8, min(64, n))
+    rho, u = workloads.random_spectrum(n, w["k0"], w["urms"], w["seed"])
+    f = oracle.init_equilibrium(rho, u)
+    beta = oracle.beta(w["nu"])
+    for _ in range(args.warmup):
+        f, _, _ = oracle.run(f, 1, beta)
+    t0 = time.perf_counter()
+    f, _, _ = oracle.run(f, args.steps, beta)
+    dt = time.perf_counter() - t0
+    value = n ** 3 * args.steps / dt / 1e6
+    sample = ("%d steps (after %d warm-up) of a %d^3 box of the hit256 field family "
+              "(random spectrum k0=4, u_rms=0.04, nu=2e-4), FP64 oracle"
+              % (args.steps, args.warmup, n))
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "MLUPS",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "hit256 field family on a bounded %d^3 sample (CPU oracle)" % n,
+                      "box": [n, n, n]},
+           "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS",
+                            "cores": oracle.num_threads(), "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return out
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=None)
+    p.add_argument("--warmup", type=int, default=None)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-variants", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    a = p.parse_args(argv)
+    if a.impl == "reference":
+        a.steps = 3 if a.steps is None else a.steps
+        a.warmup = 1 if a.warmup is None else a.warmup
+    else:
+        a.steps = 2000 if a.steps is None else a.steps
+        a.warmup = 10 if a.warmup is None else a.warmup
+        if a.warmup < 3:
+            a.warmup = 3
+    return a
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    rank, world, local = dist_init(args.gpus)
+    try:
+        if args.impl == "reference":
+            main_reference(args, rank, world)
+        else:
+            main_ours(args, rank, world, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,180 @@
+/*
+ * kbc_lb.h -- C ABI of the GB300 (sm_103a) D3Q27 KBC lattice Boltzmann library.
+ *
+ * Method: Boesch, Chikatamarla, Karlin, "Entropic multi-relaxation lattice Boltzmann scheme
+ * for turbulent flows" (arXiv:1507.02518). One time step is eq:Egeneral on a periodic box:
+ * every node collides with the KBC operator (collision listing of Sec. KBC: rho, u ->
+ * product-form equilibrium eq:entropic_eq -> shear part s from Table 1 -> ds, dh ->
+ * stabilizer gamma by eq:result21 -> f' = f - beta(2 ds + gamma dh)) and the post-collision
+ * populations propagate along the 27 links.
+ *
+ * Conventions
+ *   velocities   i = (vx+1) + 3*(vy+1) + 9*(vz+1), v in {-1,0,1}^3 (eq:D3Q27vel); the opposite
+ *                of i is 26 - i.
+ *   node index   n = x + nx*(y + ny*z) (x fastest).
+ *   canonical    a population field f[27][P] (P = nx*ny*nz, plane i contiguous) of FP64
+ *                values holding the PRE-collision populations f_i(x, t) of the current time
+ *                t. Both streaming schemes expose exactly this state.
+ *   memory       the library allocates no device memory. The caller passes one device buffer
+ *                of at least lb_required_bytes() bytes and keeps it alive until lb_destroy;
+ *                the library never frees it. "on_device" arguments say whether a pointer is
+ *                device (1) or host (0) memory; host pointers may be pageable.
+ *   streams      all work is enqueued on the CUDA stream given to lb_create (NULL = legacy
+ *                default stream). lb_step never synchronises; lb_moments, lb_diagnostics,
+ *                lb_get_populations and lb_set_populations synchronise the stream.
+ *   errors       every call returns lb_status; no exception crosses the ABI. Errors of
+ *                asynchronous kernels surface at the next synchronising call as
+ *                LB_ERR_CUDA. lb_last_error() gives a message. A context is used by one host
+ *                thread at a time.
+ */
+#ifndef KBC_LB_H
+#define KBC_LB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t lb_status;
+enum {
+  LB_OK = 0,
+  LB_ERR_INVALID_ARG = 1,  /* bad size, parameter, pointer or enum value */
+  LB_ERR_OOM = 2,          /* the buffer passed to lb_create is smaller than required */
+  LB_ERR_CUDA = 3,         /* a CUDA call or kernel failed (message in lb_last_error) */
+  LB_ERR_NONFINITE = 4,    /* lb_diagnostics found NaN/Inf populations */
+  LB_ERR_TIMEOUT = 5,      /* a bounded device-side wait ran out */
+  LB_ERR_UNSUPPORTED = 6   /* valid but not built (e.g. no sm_103a device) */
+};
+
+/* Shear part s (Sec. KBC, Table 1): s in {d, d+t, d+q, d+t+q}. */
+enum { LB_S_D = 0, LB_S_DT = 1, LB_S_DQ = 2, LB_S_DTQ = 3 };
+/* Stabilizer: eq:result21 (the method), or the fixed special cases named in Sec. KBC:
+ * gamma = 2 (LBGK) and gamma = 1/beta (regularized LB). */
+enum { LB_GAMMA_ESTIMATE = 0, LB_GAMMA_LBGK = 1, LB_GAMMA_RLB = 2 };
+/* Storage of the populations in device memory; collision arithmetic is FP64 for LB_F64 and
+ * FP32 otherwise. All three store the shift f_i - W_i; LB_F16 stores (f_i - W_i)/W_i in
+ * IEEE half precision, rounded to nearest even. */
+enum { LB_F64 = 0, LB_F32 = 1, LB_F16 = 2 };
+/* Streaming: LB_PULL keeps two population arrays (gather, collide, write);
+ * LB_AA keeps one array updated in place with alternating even/odd steps. */
+enum { LB_PULL = 0, LB_AA = 1 };
+
+typedef struct {
+  int32_t nx, ny, nz;   /* periodic box, each >= 3, nx*ny*nz < 2^31 */
+  double nu;            /* kinematic viscosity > 0; beta = 1/(6 nu + 1) (eq:viscosity, c_s^2 = 1/3) */
+  int32_t variant;      /* LB_S_* */
+  int32_t gamma_mode;   /* LB_GAMMA_* */
+  int32_t storage;      /* LB_F64 / LB_F32 / LB_F16 */
+  int32_t scheme;       /* LB_PULL / LB_AA */
+} lb_config;
+
+/* Diagnostics of Sec. "Numerical Simulations" at the current time t. Averages <.> are over
+ * nodes; u' = u - <u>; gradients are second-order central differences. */
+typedef struct {
+  int64_t step;             /* t */
+  int64_t nodes;            /* P */
+  double mass;              /* sum rho */
+  double momentum[3];       /* sum rho u */
+  double kinetic_energy;    /* k = 1/2 <u'.u'> */
+  double enstrophy;         /* Omega = 1/2 <|curl u'|^2> */
+  double dissipation;       /* epsilon = 1/2 nu <(d_b u'_a + d_a u'_b)^2> */
+  double gamma_mean;        /* <gamma> of the collision that produced the state at t */
+  double gamma_std;         /* its standard deviation over nodes */
+  int64_t nonfinite_count;  /* nodes whose rho or u is NaN/Inf */
+  int64_t den_guard_count;  /* nodes where <dh|dh> fell under the guard (gamma set to 2),
+                               counted over the same collision as gamma_mean */
+} lb_diag;
+
+typedef struct lb_ctx lb_ctx;
+
+/* Bytes of device memory a context with this configuration needs (populations, diagnostics
+ * fields and a bounded host-transfer staging area), or 0 if the configuration is invalid. */
+size_t lb_required_bytes(const lb_config *cfg);
+
+/* Create a context on the current CUDA device.
+ *   dev_buf  device buffer of `bytes` bytes, 256-byte aligned, owned by the caller.
+ *   stream   cudaStream_t to enqueue on (NULL = default stream).
+ * The populations start at rest (f_i = W_i, t = 0) until lb_init_field or
+ * lb_set_populations. On failure *out is NULL and lb_last_error(NULL) explains. */
+lb_status lb_create(const lb_config *cfg, void *dev_buf, size_t bytes, void *stream,
+                    lb_ctx **out);
+lb_status lb_destroy(lb_ctx *ctx);
+
+/* Message of the last failed call on ctx (ctx NULL: of the last failed lb_create or
+ * lb_batch_create on this thread). Never NULL; valid until the next call on ctx. */
+const char *lb_last_error(const lb_ctx *ctx);
+
+/* Set f(x, 0) = f_eq(rho(x), u(x)) by eq:entropic_eq and t = 0.
+ *   rho  FP64 [P] (NULL: rho = 1 everywhere);  u  FP64 [3][P] (u_x plane, u_y, u_z).
+ * Host inputs are copied through the staging area in chunks; |u_a| < 1 is required. */
+lb_status lb_init_field(lb_ctx *ctx, const double *rho, const double *u, int on_device);
+
+/* Advance n >= 0 time steps (eq:Egeneral with the KBC collision). Asynchronous. The last of
+ * the n collisions also records gamma per node for lb_diagnostics. */
+lb_status lb_step(lb_ctx *ctx, int64_t n);
+
+/* rho [P] and u [3][P] (FP64, caller-owned) of the current state. Synchronises. */
+lb_status lb_moments(lb_ctx *ctx, double *rho, double *u, int on_device);
+
+/* Fill *out for the current state. Synchronises. Returns LB_ERR_NONFINITE (with *out filled)
+ * if any node is NaN/Inf. */
+lb_status lb_diagnostics(lb_ctx *ctx, lb_diag *out);
+
+/* Canonical pre-collision populations f[27][P] (FP64, caller-owned) at the current time t,
+ * whatever the scheme and step parity. Synchronises. */
+lb_status lb_get_populations(lb_ctx *ctx, double *f, int on_device);
+
+/* Overwrite the state with canonical populations f[27][P] at the current time t (checkpoint
+ * resume, test seeding). Values are rounded to the storage precision. Synchronises. */
+lb_status lb_set_populations(lb_ctx *ctx, const double *f, int on_device);
+
+/* Current time t and the relaxation parameter beta of the context. */
+int64_t lb_time(const lb_ctx *ctx);
+double lb_beta(const lb_ctx *ctx);
+/* Reset t (e.g. after loading a checkpoint written at time t; call before
+ * lb_set_populations). t >= 0. */
+lb_status lb_set_time(lb_ctx *ctx, int64_t t);
+
+/* Launch shape of the step kernel: threads per block along x (bx) and y (by), with
+ * bx*by in {64, 128, 256, 512} and bx a multiple of 32. Defaults to (128, 1) or the
+ * shape the autotuner chose. */
+lb_status lb_set_block(lb_ctx *ctx, int32_t bx, int32_t by);
+
+/* ---------------------------------------------------------------- batched ensemble
+ * Many independent periodic boxes of uneven sizes and viscosities, stepped together: one
+ * kernel launch per time step walks a work list of (box, row-tile) items, and n steps are
+ * captured once in a CUDA graph and replayed. All boxes share storage, scheme, variant and
+ * gamma_mode (taken from cfgs[0]); nx/ny/nz/nu are per box. */
+typedef struct lb_batch lb_batch;
+
+size_t lb_batch_required_bytes(const lb_config *cfgs, int32_t nbox);
+lb_status lb_batch_create(const lb_config *cfgs, int32_t nbox, void *dev_buf, size_t bytes,
+                          void *stream, lb_batch **out);
+lb_status lb_batch_destroy(lb_batch *b);
+const char *lb_batch_last_error(const lb_batch *b);
+/* Per-box view: a context that aliases box `box` of the batch (init, moments, diagnostics,
+ * populations). Valid until lb_batch_destroy; do not lb_destroy it. Its lb_step steps that
+ * box alone. */
+lb_ctx *lb_batch_box(lb_batch *b, int32_t box);
+/* Advance every box n >= 0 steps by replaying the captured graph (captured on first use
+ * for this n). Asynchronous. */
+lb_status lb_batch_step(lb_batch *b, int64_t n);
+/* Diagnostics of every box into out[nbox]. Synchronises. */
+lb_status lb_batch_diagnostics(lb_batch *b, lb_diag *out);
+/* Launch shape of the batched step: `threads` per block (multiple of 32, <= 512) and `tile`,
+ * the target number of nodes per work item (an item is ceil(tile / nx) whole x-rows of one
+ * box). The grid is persistent: SMs x resident blocks, clamped to the number of items. */
+lb_status lb_batch_set_tile(lb_batch *b, int32_t threads, int32_t tile);
+/* Time each candidate (threads in {128, 256, 512}) x (tile in {256 .. 4096}) for
+ * `trial_steps` steps on the current state and keep the fastest. The state advances by the
+ * trial steps, so call it on a throw-away state (e.g. right after create) and initialise
+ * afterwards. Outputs may be NULL; best_ms is the best time per step. Synchronises. */
+lb_status lb_batch_autotune(lb_batch *b, int32_t trial_steps, int32_t *best_threads,
+                            int32_t *best_tile, double *best_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KBC_LB_H */

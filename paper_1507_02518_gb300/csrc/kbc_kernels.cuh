@@ -1,0 +1,475 @@
+// kbc_kernels.cuh -- CUDA kernels of the D3Q27 KBC step and its host-transfer helpers.
+//
+// Included once per storage type by kbc_f64.cu / kbc_f32.cu / kbc_f16.cu, which instantiate
+// kbc::Ops<S>. Hot path: step_kernel (one fused stream + KBC collide per node, eq:Egeneral)
+// and batch_kernel (the same update over a work list of boxes).
+#pragma once
+
+#include <type_traits>
+
+#include "kbc_device.cuh"
+#include "kbc_ops.h"
+
+namespace kbc {
+
+// ------------------------------------------------------------------ the fused node update
+// Loads f(x, t) of node (x, y, z) by the pattern of MODE, collides, stores f'(x) where
+// f(t+1) expects it. src and dst are the same buffer in the AA modes.
+template <typename S, int MODE, bool RECORD>
+__device__ __forceinline__ void node_update(const S* src, S* dst, const Geo& g, uint32_t x,
+                                            uint32_t y, uint32_t z, const CollideParams& cp,
+                                            float* gamma_out, StepCounters* ctr) {
+  using C = Codec<S>;
+  using R = typename C::R;
+  using Pat = Pattern<MODE>;
+  Nbr nb;
+  nb.init(g, x, y, z);
+  R d[27];
+  Unroll<0, 27>::run([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    const S* p = src + (uint64_t)Pat::load_plane(I) * g.P + nb.template at<I, Pat::load_shift>();
+    if constexpr (MODE == MODE_PULL) {
+      d[I] = C::template load_ro<I>(p);
+    } else {
+      d[I] = C::template load<I>(p);
+    }
+  });
+  bool guarded;
+  const R gamma = collide<R>(d, cp, &guarded);
+  Unroll<0, 27>::run([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    S* p = dst + (uint64_t)Pat::store_plane(I) * g.P + nb.template at<I, Pat::store_shift>();
+    C::template store<I>(p, d[I]);
+  });
+  if constexpr (RECORD) {
+    gamma_out[nb.ox[1] + nb.oy[1] + nb.oz[1]] = (float)gamma;
+    if (guarded) atomicAdd(&ctr->guarded, 1ull);
+  }
+}
+
+// FP64 arithmetic needs more than 128 registers per thread: cap its blocks at 256 threads
+template <typename S> struct MaxThreads { static constexpr int value = 512; };
+template <> struct MaxThreads<double> { static constexpr int value = 256; };
+
+template <typename S, int MODE, bool RECORD>
+__global__ void __launch_bounds__(MaxThreads<S>::value) step_kernel(const S* src, S* dst, Geo g, CollideParams cp,
+                                                   float* gamma_out, StepCounters* ctr) {
+  const uint32_t x = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t y = blockIdx.y * blockDim.y + threadIdx.y;
+  const uint32_t z = blockIdx.z;
+  if (x >= g.nx || y >= g.ny) return;
+  node_update<S, MODE, RECORD>(src, dst, g, x, y, z, cp, gamma_out, ctr);
+}
+
+// Batched ensemble: a persistent grid walks the work list; item k covers rows
+// [row0, row0 + nrows) (row = y + ny z) of one box.
+template <typename S, int MODE, bool RECORD>
+__global__ void __launch_bounds__(MaxThreads<S>::value) batch_kernel(const BoxDesc* __restrict__ boxes,
+                                                    const WorkItem* __restrict__ items,
+                                                    int nitems, int parity, int with_t,
+                                                    int with_q, int gamma_mode) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const WorkItem w = items[it];
+    const BoxDesc bd = boxes[w.box];
+    Geo g;
+    g.nx = bd.nx;
+    g.ny = bd.ny;
+    g.nz = bd.nz;
+    g.nxy = bd.nxy;
+    g.P = (uint64_t)bd.nxy * bd.nz;
+    CollideParams cp;
+    cp.beta = bd.beta;
+    cp.two_beta = bd.two_beta;
+    cp.inv_beta = bd.inv_beta;
+    cp.with_t = with_t;
+    cp.with_q = with_q;
+    cp.gamma_mode = gamma_mode;
+    const S* src = (const S*)bd.pop[MODE == MODE_PULL ? parity : 0];
+    S* dst = (S*)bd.pop[MODE == MODE_PULL ? (parity ^ 1) : 0];
+    const uint32_t nodes = bd.nx * (uint32_t)w.nrows;
+    for (uint32_t k = threadIdx.x; k < nodes; k += blockDim.x) {
+      const uint32_t row = (uint32_t)w.row0 + k / bd.nx;
+      const uint32_t x = k - (k / bd.nx) * bd.nx;
+      const uint32_t z = row / bd.ny;
+      const uint32_t y = row - z * bd.ny;
+      node_update<S, MODE, RECORD>(src, dst, g, x, y, z, cp, bd.gamma, bd.ctr);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ canonical addressing
+// Address of canonical population i of node (x, y, z) at a time of the given parity.
+template <typename S>
+__device__ __forceinline__ S* canon_addr(S* b0, S* b1, const Geo& g, const Nbr& nb, int scheme,
+                                         int parity, int i) {
+  const uint32_t back = nb.ox[1 - cx(i)] + nb.oy[1 - cy(i)] + nb.oz[1 - cz(i)];
+  const uint32_t here = nb.ox[1] + nb.oy[1] + nb.oz[1];
+  if (scheme == 0) return (parity ? b1 : b0) + (uint64_t)i * g.P + back;
+  if (parity == 0) return b0 + (uint64_t)i * g.P + here;
+  return b0 + (uint64_t)(26 - i) * g.P + back;
+}
+
+__device__ __forceinline__ void node_coords(const Geo& g, uint64_t n, uint32_t& x, uint32_t& y,
+                                            uint32_t& z) {
+  z = (uint32_t)(n / g.nxy);
+  const uint32_t r = (uint32_t)(n - (uint64_t)z * g.nxy);
+  y = r / g.nx;
+  x = r - y * g.nx;
+}
+
+template <typename S>
+__global__ void init_kernel(S* b0, S* b1, Geo g, int scheme, int parity, const double* rho,
+                            const double* u, uint64_t n0, uint64_t cnt, uint64_t ld) {
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < cnt;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t x, y, z;
+    node_coords(g, n0 + k, x, y, z);
+    Nbr nb;
+    nb.init(g, x, y, z);
+    double dq[27];
+    equilibrium_shift(rho ? rho[k] : 1.0, u[k], u[ld + k], u[2 * ld + k], dq);
+#pragma unroll
+    for (int i = 0; i < 27; ++i)
+      *canon_addr<S>(b0, b1, g, nb, scheme, parity, i) = Codec<S>::from_delta(dq[i], i);
+  }
+}
+
+template <typename S>
+__global__ void get_kernel(const S* b0, const S* b1, Geo g, int scheme, int parity, double* out,
+                           uint64_t n0, uint64_t cnt, uint64_t ld) {
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < cnt;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t x, y, z;
+    node_coords(g, n0 + k, x, y, z);
+    Nbr nb;
+    nb.init(g, x, y, z);
+#pragma unroll
+    for (int i = 0; i < 27; ++i) {
+      const S v = *canon_addr<S>((S*)b0, (S*)b1, g, nb, scheme, parity, i);
+      out[i * ld + k] = wgt(i) + Codec<S>::to_delta(v, i);
+    }
+  }
+}
+
+template <typename S>
+__global__ void set_kernel(S* b0, S* b1, Geo g, int scheme, int parity, const double* in,
+                           uint64_t n0, uint64_t cnt, uint64_t ld) {
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < cnt;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t x, y, z;
+    node_coords(g, n0 + k, x, y, z);
+    Nbr nb;
+    nb.init(g, x, y, z);
+#pragma unroll
+    for (int i = 0; i < 27; ++i)
+      *canon_addr<S>(b0, b1, g, nb, scheme, parity, i) =
+          Codec<S>::from_delta(in[i * ld + k] - wgt(i), i);
+  }
+}
+
+// rho and rho u of canonical f(t) at one node, accumulated in FP64 from the shifts
+template <typename S>
+__device__ __forceinline__ void node_moments(const S* b0, const S* b1, const Geo& g,
+                                             const Nbr& nb, int scheme, int parity, double& rho,
+                                             double (&m)[3]) {
+  double s = 0.0, mx = 0.0, my = 0.0, mz = 0.0;
+#pragma unroll
+  for (int i = 0; i < 27; ++i) {
+    const double dv = Codec<S>::to_delta(*canon_addr<S>((S*)b0, (S*)b1, g, nb, scheme, parity, i), i);
+    s += dv;
+    if (cx(i)) mx += cx(i) * dv;
+    if (cy(i)) my += cy(i) * dv;
+    if (cz(i)) mz += cz(i) * dv;
+  }
+  rho = 1.0 + s;
+  m[0] = mx;
+  m[1] = my;
+  m[2] = mz;
+}
+
+template <typename S>
+__global__ void moments_kernel(const S* b0, const S* b1, Geo g, int scheme, int parity,
+                               double* rho_out, double* u_out, uint64_t n0, uint64_t cnt,
+                               uint64_t ld) {
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < cnt;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t x, y, z;
+    node_coords(g, n0 + k, x, y, z);
+    Nbr nb;
+    nb.init(g, x, y, z);
+    double rho, m[3];
+    node_moments<S>(b0, b1, g, nb, scheme, parity, rho, m);
+    if (rho_out) rho_out[k] = rho;
+    for (int a = 0; a < 3; ++a) u_out[a * ld + k] = m[a] / rho;
+  }
+}
+
+// ------------------------------------------------------------------ diagnostics
+// Sums (FP64) in partials[block * kDiagSums + j]:
+//  0 sum rho, 1-3 sum rho u, 4-6 sum u, 7 sum |u|^2, 8 sum gamma, 9 sum gamma^2,
+//  10 non-finite nodes, 11 sum |curl u|^2, 12 sum (d_b u_a + d_a u_b)^2
+template <int N>
+__device__ __forceinline__ void block_reduce_store(double (&v)[N], double* dst) {
+  __shared__ double sh[32][N];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
+  }
+  if (lane == 0)
+    for (int j = 0; j < N; ++j) sh[warp][j] = v[j];
+  __syncthreads();
+  if (threadIdx.x < N) {
+    double acc = 0.0;
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int w = 0; w < nw; ++w) acc += sh[w][threadIdx.x];
+    dst[threadIdx.x] = acc;
+  }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256) diag_fields_kernel(const S* b0, const S* b1, Geo g,
+                                                          int scheme, int parity,
+                                                          const float* gamma, int with_gamma,
+                                                          typename Codec<S>::R* uf,
+                                                          double* partials) {
+  using R = typename Codec<S>::R;
+  double v[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (uint64_t n = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; n < g.P;
+       n += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t x, y, z;
+    node_coords(g, n, x, y, z);
+    Nbr nb;
+    nb.init(g, x, y, z);
+    double rho, m[3];
+    node_moments<S>(b0, b1, g, nb, scheme, parity, rho, m);
+    const double ux = m[0] / rho, uy = m[1] / rho, uz = m[2] / rho;
+    uf[n] = (R)ux;
+    uf[g.P + n] = (R)uy;
+    uf[2 * g.P + n] = (R)uz;
+    if (!isfinite(rho) || !isfinite(ux) || !isfinite(uy) || !isfinite(uz)) {
+      v[10] += 1.0;
+      continue;
+    }
+    v[0] += rho;
+    v[1] += m[0];
+    v[2] += m[1];
+    v[3] += m[2];
+    v[4] += ux;
+    v[5] += uy;
+    v[6] += uz;
+    v[7] += ux * ux + uy * uy + uz * uz;
+    if (with_gamma) {
+      const double gm = gamma[n];
+      v[8] += gm;
+      v[9] += gm * gm;
+    }
+  }
+  block_reduce_store<11>(v, partials + blockIdx.x * kDiagSums);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) diag_grad_kernel(Geo g, const R* uf, double* partials) {
+  double v[2] = {0.0, 0.0};
+  for (uint64_t n = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; n < g.P;
+       n += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t x, y, z;
+    node_coords(g, n, x, y, z);
+    Nbr nb;
+    nb.init(g, x, y, z);
+    const uint32_t here = nb.ox[1] + nb.oy[1] + nb.oz[1];
+    // neighbours along +-x, +-y, +-z
+    const uint32_t np[3] = {nb.ox[2] + nb.oy[1] + nb.oz[1], nb.ox[1] + nb.oy[2] + nb.oz[1],
+                            nb.ox[1] + nb.oy[1] + nb.oz[2]};
+    const uint32_t nm[3] = {nb.ox[0] + nb.oy[1] + nb.oz[1], nb.ox[1] + nb.oy[0] + nb.oz[1],
+                            nb.ox[1] + nb.oy[1] + nb.oz[0]};
+    (void)here;
+    double gr[3][3];  // gr[a][b] = d u_a / d x_b, second-order central difference
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+        gr[a][b] = 0.5 * ((double)uf[a * g.P + np[b]] - (double)uf[a * g.P + nm[b]]);
+    const double wx = gr[2][1] - gr[1][2], wy = gr[0][2] - gr[2][0], wz = gr[1][0] - gr[0][1];
+    const double ww = wx * wx + wy * wy + wz * wz;
+    double ss = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const double s = gr[a][b] + gr[b][a];
+        ss += s * s;
+      }
+    if (isfinite(ww) && isfinite(ss)) {
+      v[0] += ww;
+      v[1] += ss;
+    }
+  }
+  block_reduce_store<2>(v, partials + blockIdx.x * kDiagSums + 11);
+}
+
+// fixed-order final reduction: sums[j] = sum over blocks of partials[block][j]
+static __global__ void diag_final_kernel(const double* partials, int nblocks, double* sums) {
+  const int j = threadIdx.x;
+  if (j >= kDiagSums) return;
+  double acc = 0.0;
+  for (int b = 0; b < nblocks; ++b) acc += partials[b * kDiagSums + j];
+  sums[j] = acc;
+}
+
+// ------------------------------------------------------------------ host launchers
+inline Geo make_geo(const BoxView& b) {
+  Geo g;
+  g.nx = b.nx;
+  g.ny = b.ny;
+  g.nz = b.nz;
+  g.nxy = b.nx * b.ny;
+  g.P = b.P;
+  return g;
+}
+
+inline CollideParams make_cp(double beta, int with_t, int with_q, int gamma_mode) {
+  CollideParams cp;
+  cp.beta = beta;
+  cp.two_beta = 2.0 * beta;
+  cp.inv_beta = 1.0 / beta;
+  cp.with_t = with_t;
+  cp.with_q = with_q;
+  cp.gamma_mode = gamma_mode;
+  return cp;
+}
+
+inline int grid_for(uint64_t cnt, int threads) {
+  uint64_t blocks = (cnt + threads - 1) / threads;
+  const uint64_t cap = 152ull * 16;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  return (int)blocks;
+}
+
+template <typename S>
+cudaError_t Ops<S>::step(const BoxView& b, int64_t t, bool record, int bx, int by,
+                         StepCounters* counters, cudaStream_t st) {
+  const Geo g = make_geo(b);
+  const CollideParams cp = make_cp(b.beta, b.with_t, b.with_q, b.gamma_mode);
+  const dim3 block(bx, by, 1);
+  const dim3 grid((b.nx + bx - 1) / bx, (b.ny + by - 1) / by, b.nz);
+  const int parity = (int)(t & 1);
+  if (b.scheme == 0) {
+    const S* src = (const S*)b.pop[parity];
+    S* dst = (S*)b.pop[parity ^ 1];
+    if (record)
+      step_kernel<S, MODE_PULL, true><<<grid, block, 0, st>>>(src, dst, g, cp, b.gamma, counters);
+    else
+      step_kernel<S, MODE_PULL, false><<<grid, block, 0, st>>>(src, dst, g, cp, b.gamma, counters);
+  } else {
+    S* buf = (S*)b.pop[0];
+    if (parity == 0) {
+      if (record)
+        step_kernel<S, MODE_AA_EVEN, true><<<grid, block, 0, st>>>(buf, buf, g, cp, b.gamma, counters);
+      else
+        step_kernel<S, MODE_AA_EVEN, false><<<grid, block, 0, st>>>(buf, buf, g, cp, b.gamma, counters);
+    } else {
+      if (record)
+        step_kernel<S, MODE_AA_ODD, true><<<grid, block, 0, st>>>(buf, buf, g, cp, b.gamma, counters);
+      else
+        step_kernel<S, MODE_AA_ODD, false><<<grid, block, 0, st>>>(buf, buf, g, cp, b.gamma, counters);
+    }
+  }
+  return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t Ops<S>::init(const BoxView& b, int64_t t, const double* rho, const double* u,
+                         uint64_t n0, uint64_t cnt, uint64_t ld, cudaStream_t st) {
+  init_kernel<S><<<grid_for(cnt, 256), 256, 0, st>>>((S*)b.pop[0], (S*)b.pop[1], make_geo(b),
+                                                     b.scheme, (int)(t & 1), rho, u, n0, cnt, ld);
+  return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t Ops<S>::get(const BoxView& b, int64_t t, double* out, uint64_t n0, uint64_t cnt,
+                        uint64_t ld, cudaStream_t st) {
+  get_kernel<S><<<grid_for(cnt, 256), 256, 0, st>>>((const S*)b.pop[0], (const S*)b.pop[1],
+                                                    make_geo(b), b.scheme, (int)(t & 1), out, n0,
+                                                    cnt, ld);
+  return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t Ops<S>::set(const BoxView& b, int64_t t, const double* in, uint64_t n0,
+                        uint64_t cnt, uint64_t ld, cudaStream_t st) {
+  set_kernel<S><<<grid_for(cnt, 256), 256, 0, st>>>((S*)b.pop[0], (S*)b.pop[1], make_geo(b),
+                                                    b.scheme, (int)(t & 1), in, n0, cnt, ld);
+  return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t Ops<S>::moments(const BoxView& b, int64_t t, double* rho, double* u, uint64_t n0,
+                            uint64_t cnt, uint64_t ld, cudaStream_t st) {
+  moments_kernel<S><<<grid_for(cnt, 256), 256, 0, st>>>((const S*)b.pop[0], (const S*)b.pop[1],
+                                                        make_geo(b), b.scheme, (int)(t & 1), rho,
+                                                        u, n0, cnt, ld);
+  return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t Ops<S>::diag(const BoxView& b, int64_t t, bool with_gamma, void* ufield,
+                         double* partials, int nblocks, double* sums, cudaStream_t st) {
+  using R = typename Codec<S>::R;
+  const Geo g = make_geo(b);
+  cudaMemsetAsync(partials, 0, sizeof(double) * kDiagSums * nblocks, st);
+  diag_fields_kernel<S><<<nblocks, 256, 0, st>>>((const S*)b.pop[0], (const S*)b.pop[1], g,
+                                                 b.scheme, (int)(t & 1), b.gamma,
+                                                 with_gamma ? 1 : 0, (R*)ufield, partials);
+  diag_grad_kernel<R><<<nblocks, 256, 0, st>>>(g, (const R*)ufield, partials);
+  diag_final_kernel<<<1, 32, 0, st>>>(partials, nblocks, sums);
+  return cudaGetLastError();
+}
+
+template <typename S, int MODE>
+static void launch_batch(const BoxDesc* boxes, const WorkItem* items, int nitems, int parity,
+                         bool record, int with_t, int with_q, int gamma_mode, int threads,
+                         int grid, cudaStream_t st) {
+  if (record)
+    batch_kernel<S, MODE, true><<<grid, threads, 0, st>>>(boxes, items, nitems, parity, with_t,
+                                                          with_q, gamma_mode);
+  else
+    batch_kernel<S, MODE, false><<<grid, threads, 0, st>>>(boxes, items, nitems, parity, with_t,
+                                                           with_q, gamma_mode);
+}
+
+template <typename S>
+cudaError_t Ops<S>::batch_step(const BoxDesc* boxes, const WorkItem* items, int nitems,
+                               int64_t t, bool record, int scheme, int with_t, int with_q,
+                               int gamma_mode, int threads, int grid, cudaStream_t st) {
+  const int parity = (int)(t & 1);
+  if (scheme == 0)
+    launch_batch<S, MODE_PULL>(boxes, items, nitems, parity, record, with_t, with_q, gamma_mode,
+                               threads, grid, st);
+  else if (parity == 0)
+    launch_batch<S, MODE_AA_EVEN>(boxes, items, nitems, parity, record, with_t, with_q,
+                                  gamma_mode, threads, grid, st);
+  else
+    launch_batch<S, MODE_AA_ODD>(boxes, items, nitems, parity, record, with_t, with_q,
+                                 gamma_mode, threads, grid, st);
+  return cudaGetLastError();
+}
+
+template <typename S>
+int Ops<S>::batch_occupancy(int threads, int scheme) {
+  int blocks = 0;
+  cudaError_t e;
+  if (scheme == 0)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, batch_kernel<S, MODE_PULL, false>,
+                                                      threads, 0);
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks,
+                                                      batch_kernel<S, MODE_AA_ODD, false>,
+                                                      threads, 0);
+  if (e != cudaSuccess || blocks < 1) blocks = 1;
+  return blocks;
+}
+
+}  // namespace kbc

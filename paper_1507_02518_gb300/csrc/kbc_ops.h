@@ -1,0 +1,71 @@
+// kbc_ops.h -- host-side launch interface of the per-storage kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace kbc {
+
+struct BoxView {
+  uint32_t nx, ny, nz;
+  uint64_t P;          // nx * ny * nz
+  void* pop[2];        // population buffers (pull: two; AA: pop[1] == pop[0])
+  float* gamma;        // [P] stabilizer of the last recorded collision
+  double beta;
+  int with_t, with_q, gamma_mode;
+  int scheme;          // 0 pull, 1 AA
+};
+
+// counters written by the step kernel when it records gamma
+struct StepCounters {
+  unsigned long long guarded;
+};
+
+// one item of the batched work list: rows [row0, row0 + nrows) of box `box`
+// (row = y + ny * z)
+struct WorkItem {
+  int32_t box;
+  int32_t row0;
+  int32_t nrows;
+  int32_t pad;
+};
+
+// device-side description of one box of a batch
+struct BoxDesc {
+  uint32_t nx, ny, nz, nxy;
+  void* pop[2];
+  float* gamma;
+  StepCounters* ctr;
+  double beta, two_beta, inv_beta;
+};
+
+template <typename S> struct Ops {
+  // one time step t -> t+1 of one box; `record` writes gamma and counts guards
+  static cudaError_t step(const BoxView& b, int64_t t, bool record, int bx, int by,
+                          StepCounters* counters, cudaStream_t st);
+  // canonical f(t) = f_eq(rho, u) for nodes [n0, n0 + cnt) (rho may be null: 1)
+  static cudaError_t init(const BoxView& b, int64_t t, const double* rho, const double* u,
+                          uint64_t n0, uint64_t cnt, uint64_t ld, cudaStream_t st);
+  // out[i * ld + (n - n0)] = canonical f_i(n, t) for n in [n0, n0 + cnt)
+  static cudaError_t get(const BoxView& b, int64_t t, double* out, uint64_t n0, uint64_t cnt,
+                         uint64_t ld, cudaStream_t st);
+  static cudaError_t set(const BoxView& b, int64_t t, const double* in, uint64_t n0,
+                         uint64_t cnt, uint64_t ld, cudaStream_t st);
+  // rho[n - n0], u[a * ld + (n - n0)] of f(t)
+  static cudaError_t moments(const BoxView& b, int64_t t, double* rho, double* u, uint64_t n0,
+                             uint64_t cnt, uint64_t ld, cudaStream_t st);
+  // diagnostics: writes u (arithmetic type of S) to ufield[3][P] and per-block partial sums
+  static cudaError_t diag(const BoxView& b, int64_t t, bool with_gamma, void* ufield,
+                          double* partials, int nblocks, double* sums, cudaStream_t st);
+  // one time step of every box of a batch over a work list
+  static cudaError_t batch_step(const BoxDesc* boxes, const WorkItem* items, int nitems,
+                                int64_t t, bool record, int scheme, int with_t, int with_q,
+                                int gamma_mode, int threads, int grid, cudaStream_t st);
+  // resident blocks per SM of the batch kernel at this block size
+  static int batch_occupancy(int threads, int scheme);
+};
+
+constexpr int kDiagSums = 16;   // layout of the diagnostics sums, see kbc_kernels.cuh
+constexpr int kDiagBlocks = 608;  // fixed grid of the reduction kernels (4 per SM on 152 SMs)
+
+}  // namespace kbc

@@ -1,0 +1,869 @@
+// lb_api.cu -- C ABI of the KBC library (see include/kbc_lb.h): context management, bounded
+// host staging, diagnostics assembly and the batched ensemble with its CUDA graphs and
+// launch-shape autotuner. The library allocates no device memory: every region below is
+// carved out of the caller's buffer.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "kbc_lb.h"
+#include "kbc_ops.h"
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr size_t kAlign = 256;
+constexpr uint64_t kStageNodes = 1ull << 20;  // host-transfer chunk (nodes)
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+size_t elem_size(int storage) { return storage == LB_F64 ? 8 : (storage == LB_F32 ? 4 : 2); }
+size_t arith_size(int storage) { return storage == LB_F64 ? 8 : 4; }
+
+bool valid_config(const lb_config* c, std::string* why) {
+  char buf[256];
+  if (!c) {
+    *why = "config is NULL";
+    return false;
+  }
+  if (c->nx < 3 || c->ny < 3 || c->nz < 3) {
+    snprintf(buf, sizeof buf, "box %d x %d x %d: every edge must be >= 3", c->nx, c->ny, c->nz);
+    *why = buf;
+    return false;
+  }
+  const uint64_t P = (uint64_t)c->nx * c->ny * c->nz;
+  if (P >= (1ull << 31)) {
+    *why = "nx*ny*nz must be < 2^31";
+    return false;
+  }
+  if (!(c->nu > 0.0) || !std::isfinite(c->nu)) {
+    *why = "nu must be finite and > 0";
+    return false;
+  }
+  if (c->variant < LB_S_D || c->variant > LB_S_DTQ) {
+    *why = "variant must be LB_S_D..LB_S_DTQ";
+    return false;
+  }
+  if (c->gamma_mode < LB_GAMMA_ESTIMATE || c->gamma_mode > LB_GAMMA_RLB) {
+    *why = "gamma_mode must be LB_GAMMA_ESTIMATE, LB_GAMMA_LBGK or LB_GAMMA_RLB";
+    return false;
+  }
+  if (c->storage < LB_F64 || c->storage > LB_F16) {
+    *why = "storage must be LB_F64, LB_F32 or LB_F16";
+    return false;
+  }
+  if (c->scheme != LB_PULL && c->scheme != LB_AA) {
+    *why = "scheme must be LB_PULL or LB_AA";
+    return false;
+  }
+  return true;
+}
+
+// per-box region: populations (1 or 2 arrays), gamma field, step counters
+struct BoxLayout {
+  size_t pop0, pop1, gamma, counters, total;
+};
+BoxLayout box_layout(const lb_config* c, size_t off) {
+  const uint64_t P = (uint64_t)c->nx * c->ny * c->nz;
+  BoxLayout L;
+  L.pop0 = off = align_up(off);
+  off += 27 * P * elem_size(c->storage);
+  if (c->scheme == LB_PULL) {
+    L.pop1 = off = align_up(off);
+    off += 27 * P * elem_size(c->storage);
+  } else {
+    L.pop1 = L.pop0;
+  }
+  L.gamma = off = align_up(off);
+  off += P * sizeof(float);
+  L.counters = off = align_up(off);
+  off += sizeof(kbc::StepCounters);
+  L.total = align_up(off);
+  return L;
+}
+
+// shared work region: diagnostics velocity field, partial sums, staging
+struct SharedLayout {
+  size_t ufield, partials, sums, staging, total;
+  uint64_t stage_nodes;
+};
+SharedLayout shared_layout(int storage, uint64_t maxP, size_t off) {
+  SharedLayout L;
+  L.ufield = off = align_up(off);
+  off += 3 * maxP * arith_size(storage);
+  L.partials = off = align_up(off);
+  off += sizeof(double) * kbc::kDiagSums * kbc::kDiagBlocks;
+  L.sums = off = align_up(off);
+  off += sizeof(double) * kbc::kDiagSums;
+  L.stage_nodes = maxP < kStageNodes ? maxP : kStageNodes;
+  L.staging = off = align_up(off);
+  off += L.stage_nodes * 27 * sizeof(double);
+  L.total = align_up(off);
+  return L;
+}
+
+lb_status check_device(std::string* why) {
+  int dev = 0, major = 0, minor = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  if (e != cudaSuccess) {
+    *why = std::string("no usable CUDA device: ") + cudaGetErrorString(e);
+    return LB_ERR_CUDA;
+  }
+  if (major != 10 || minor != 3) {
+    char buf[128];
+    snprintf(buf, sizeof buf, "kernels are built for sm_103a only; device is sm_%d%d", major,
+             minor);
+    *why = buf;
+    return LB_ERR_UNSUPPORTED;
+  }
+  return LB_OK;
+}
+
+}  // namespace
+
+struct lb_ctx {
+  lb_config cfg;
+  kbc::BoxView box;
+  int64_t t = 0;
+  cudaStream_t stream = nullptr;
+  void* ufield = nullptr;
+  double* partials = nullptr;
+  double* sums = nullptr;
+  kbc::StepCounters* counters = nullptr;
+  double* staging = nullptr;
+  uint64_t stage_nodes = 0;
+  int bx = 128, by = 1;
+  bool gamma_valid = false;
+  bool batch_view = false;
+  std::string err;
+};
+
+namespace {
+
+lb_status fail(lb_ctx* c, lb_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+lb_status cuda_fail(lb_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, LB_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void default_block(lb_ctx* c) {
+  int bx = 128;
+  while (bx > 32 && bx / 2 >= c->cfg.nx) bx /= 2;
+  c->bx = bx;
+  c->by = 128 / bx;
+}
+
+void setup_ctx(lb_ctx* c, const lb_config* cfg, char* base, const BoxLayout& B,
+               const SharedLayout& S, cudaStream_t st) {
+  c->cfg = *cfg;
+  c->box.nx = cfg->nx;
+  c->box.ny = cfg->ny;
+  c->box.nz = cfg->nz;
+  c->box.P = (uint64_t)cfg->nx * cfg->ny * cfg->nz;
+  c->box.pop[0] = base + B.pop0;
+  c->box.pop[1] = base + B.pop1;
+  c->box.gamma = (float*)(base + B.gamma);
+  c->box.beta = 1.0 / (6.0 * cfg->nu + 1.0);  // eq:viscosity with c_s^2 = 1/3
+  c->box.with_t = (cfg->variant == LB_S_DT || cfg->variant == LB_S_DTQ);
+  c->box.with_q = (cfg->variant == LB_S_DQ || cfg->variant == LB_S_DTQ);
+  c->box.gamma_mode = cfg->gamma_mode;
+  c->box.scheme = cfg->scheme;
+  c->counters = (kbc::StepCounters*)(base + B.counters);
+  c->stream = st;
+  c->ufield = base + S.ufield;
+  c->partials = (double*)(base + S.partials);
+  c->sums = (double*)(base + S.sums);
+  c->staging = (double*)(base + S.staging);
+  c->stage_nodes = S.stage_nodes;
+  default_block(c);
+}
+
+// dispatch a member of Ops<S> on the context's storage type
+template <typename F> cudaError_t dispatch(const lb_ctx* c, F&& f) {
+  switch (c->cfg.storage) {
+    case LB_F64: return f(kbc::Ops<double>{});
+    case LB_F32: return f(kbc::Ops<float>{});
+    default: return f(kbc::Ops<uint16_t>{});
+  }
+}
+
+lb_status zero_state(lb_ctx* c) {
+  const size_t bytes = 27 * c->box.P * elem_size(c->cfg.storage);
+  cudaError_t e = cudaMemsetAsync(c->box.pop[0], 0, bytes, c->stream);
+  if (e == cudaSuccess && c->box.pop[1] != c->box.pop[0])
+    e = cudaMemsetAsync(c->box.pop[1], 0, bytes, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->counters, 0, sizeof(kbc::StepCounters), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "clearing populations");
+  c->t = 0;
+  c->gamma_valid = false;
+  return LB_OK;
+}
+
+lb_status sync(lb_ctx* c, const char* what) {
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, what);
+  return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lb_required_bytes(const lb_config* cfg) {
+  std::string why;
+  if (!valid_config(cfg, &why)) return 0;
+  const BoxLayout B = box_layout(cfg, 0);
+  const SharedLayout S = shared_layout(cfg->storage, (uint64_t)cfg->nx * cfg->ny * cfg->nz, B.total);
+  return S.total;
+}
+
+lb_status lb_create(const lb_config* cfg, void* dev_buf, size_t bytes, void* stream,
+                    lb_ctx** out) {
+  if (!out) {
+    g_create_error = "out is NULL";
+    return LB_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  std::string why;
+  if (!valid_config(cfg, &why)) {
+    g_create_error = why;
+    return LB_ERR_INVALID_ARG;
+  }
+  if (!dev_buf || ((uintptr_t)dev_buf % kAlign) != 0) {
+    g_create_error = "dev_buf must be a non-NULL 256-byte aligned device pointer";
+    return LB_ERR_INVALID_ARG;
+  }
+  const size_t need = lb_required_bytes(cfg);
+  if (bytes < need) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "buffer of %zu bytes is smaller than the %zu bytes required", bytes,
+             need);
+    g_create_error = buf;
+    return LB_ERR_OOM;
+  }
+  lb_status s = check_device(&why);
+  if (s != LB_OK) {
+    g_create_error = why;
+    return s;
+  }
+  lb_ctx* c = new lb_ctx();
+  char* base = (char*)dev_buf;
+  const BoxLayout B = box_layout(cfg, 0);
+  const SharedLayout S = shared_layout(cfg->storage, (uint64_t)cfg->nx * cfg->ny * cfg->nz, B.total);
+  setup_ctx(c, cfg, base, B, S, (cudaStream_t)stream);
+  s = zero_state(c);
+  if (s != LB_OK) {
+    g_create_error = c->err;
+    delete c;
+    return s;
+  }
+  *out = c;
+  return LB_OK;
+}
+
+lb_status lb_destroy(lb_ctx* c) {
+  if (!c) return LB_ERR_INVALID_ARG;
+  if (c->batch_view) return fail(c, LB_ERR_INVALID_ARG, "a batch box view is owned by its batch");
+  delete c;
+  return LB_OK;
+}
+
+const char* lb_last_error(const lb_ctx* c) {
+  return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+lb_status lb_init_field(lb_ctx* c, const double* rho, const double* u, int on_device) {
+  if (!c) return LB_ERR_INVALID_ARG;
+  if (!u) return fail(c, LB_ERR_INVALID_ARG, "u is NULL");
+  const uint64_t P = c->box.P;
+  c->t = 0;
+  c->gamma_valid = false;
+  cudaError_t e;
+  if (on_device) {
+    e = dispatch(c, [&](auto ops) { return ops.init(c->box, 0, rho, u, 0, P, P, c->stream); });
+    if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
+    return LB_OK;
+  }
+  for (uint64_t n0 = 0; n0 < P; n0 += c->stage_nodes) {
+    const uint64_t cnt = (P - n0 < c->stage_nodes) ? P - n0 : c->stage_nodes;
+    double* srho = c->staging;
+    double* su = c->staging + cnt;
+    e = cudaSuccess;
+    if (rho) e = cudaMemcpyAsync(srho, rho + n0, cnt * 8, cudaMemcpyHostToDevice, c->stream);
+    for (int a = 0; a < 3 && e == cudaSuccess; ++a)
+      e = cudaMemcpyAsync(su + a * cnt, u + a * P + n0, cnt * 8, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "copying initial fields");
+    e = dispatch(c, [&](auto ops) {
+      return ops.init(c->box, 0, rho ? srho : nullptr, su, n0, cnt, cnt, c->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
+  }
+  return sync(c, "init");
+}
+
+lb_status lb_step(lb_ctx* c, int64_t n) {
+  if (!c) return LB_ERR_INVALID_ARG;
+  if (n < 0) return fail(c, LB_ERR_INVALID_ARG, "n must be >= 0");
+  for (int64_t k = 0; k < n; ++k) {
+    const bool record = (k == n - 1);
+    cudaError_t e = cudaSuccess;
+    if (record) e = cudaMemsetAsync(c->counters, 0, sizeof(kbc::StepCounters), c->stream);
+    if (e == cudaSuccess)
+      e = dispatch(c, [&](auto ops) {
+        return ops.step(c->box, c->t, record, c->bx, c->by, c->counters, c->stream);
+      });
+    if (e != cudaSuccess) return cuda_fail(c, e, "step kernel");
+    c->t += 1;
+  }
+  if (n > 0) c->gamma_valid = true;
+  return LB_OK;
+}
+
+lb_status lb_moments(lb_ctx* c, double* rho, double* u, int on_device) {
+  if (!c) return LB_ERR_INVALID_ARG;
+  if (!u) return fail(c, LB_ERR_INVALID_ARG, "u is NULL");
+  const uint64_t P = c->box.P;
+  cudaError_t e;
+  if (on_device) {
+    e = dispatch(c, [&](auto ops) { return ops.moments(c->box, c->t, rho, u, 0, P, P, c->stream); });
+    if (e != cudaSuccess) return cuda_fail(c, e, "moments kernel");
+    return sync(c, "moments");
+  }
+  for (uint64_t n0 = 0; n0 < P; n0 += c->stage_nodes) {
+    const uint64_t cnt = (P - n0 < c->stage_nodes) ? P - n0 : c->stage_nodes;
+    double* srho = c->staging;
+    double* su = c->staging + cnt;
+    e = dispatch(c, [&](auto ops) {
+      return ops.moments(c->box, c->t, srho, su, n0, cnt, cnt, c->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(c, e, "moments kernel");
+    if (rho) e = cudaMemcpyAsync(rho + n0, srho, cnt * 8, cudaMemcpyDeviceToHost, c->stream);
+    for (int a = 0; a < 3 && e == cudaSuccess; ++a)
+      e = cudaMemcpyAsync(u + a * P + n0, su + a * cnt, cnt * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "copying moments");
+  }
+  return sync(c, "moments");
+}
+
+lb_status lb_diagnostics(lb_ctx* c, lb_diag* out) {
+  if (!c || !out) return c ? fail(c, LB_ERR_INVALID_ARG, "out is NULL") : LB_ERR_INVALID_ARG;
+  cudaError_t e = dispatch(c, [&](auto ops) {
+    return ops.diag(c->box, c->t, c->gamma_valid, c->ufield, c->partials, kbc::kDiagBlocks,
+                    c->sums, c->stream);
+  });
+  if (e != cudaSuccess) return cuda_fail(c, e, "diagnostics kernels");
+  double s[kbc::kDiagSums];
+  kbc::StepCounters ctr;
+  e = cudaMemcpyAsync(s, c->sums, sizeof s, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&ctr, c->counters, sizeof ctr, cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "copying diagnostics");
+  lb_status st = sync(c, "diagnostics");
+  if (st != LB_OK) return st;
+  const double P = (double)c->box.P;
+  out->step = c->t;
+  out->nodes = (int64_t)c->box.P;
+  out->mass = s[0];
+  for (int a = 0; a < 3; ++a) out->momentum[a] = s[1 + a];
+  const double mx = s[4] / P, my = s[5] / P, mz = s[6] / P;
+  out->kinetic_energy = 0.5 * (s[7] / P - (mx * mx + my * my + mz * mz));
+  out->enstrophy = 0.5 * s[11] / P;
+  out->dissipation = 0.5 * c->cfg.nu * s[12] / P;
+  if (c->gamma_valid) {
+    const double gm = s[8] / P;
+    const double var = s[9] / P - gm * gm;
+    out->gamma_mean = gm;
+    out->gamma_std = var > 0.0 ? std::sqrt(var) : 0.0;
+    out->den_guard_count = (int64_t)ctr.guarded;
+  } else {
+    out->gamma_mean = NAN;
+    out->gamma_std = NAN;
+    out->den_guard_count = 0;
+  }
+  out->nonfinite_count = (int64_t)s[10];
+  if (out->nonfinite_count > 0) {
+    char buf[96];
+    snprintf(buf, sizeof buf, "%lld nodes hold NaN/Inf at step %lld",
+             (long long)out->nonfinite_count, (long long)c->t);
+    return fail(c, LB_ERR_NONFINITE, buf);
+  }
+  return LB_OK;
+}
+
+lb_status lb_get_populations(lb_ctx* c, double* f, int on_device) {
+  if (!c) return LB_ERR_INVALID_ARG;
+  if (!f) return fail(c, LB_ERR_INVALID_ARG, "f is NULL");
+  const uint64_t P = c->box.P;
+  cudaError_t e;
+  if (on_device) {
+    e = dispatch(c, [&](auto ops) { return ops.get(c->box, c->t, f, 0, P, P, c->stream); });
+    if (e != cudaSuccess) return cuda_fail(c, e, "export kernel");
+    return sync(c, "get_populations");
+  }
+  for (uint64_t n0 = 0; n0 < P; n0 += c->stage_nodes) {
+    const uint64_t cnt = (P - n0 < c->stage_nodes) ? P - n0 : c->stage_nodes;
+    e = dispatch(c, [&](auto ops) { return ops.get(c->box, c->t, c->staging, n0, cnt, cnt, c->stream); });
+    if (e != cudaSuccess) return cuda_fail(c, e, "export kernel");
+    for (int i = 0; i < 27 && e == cudaSuccess; ++i)
+      e = cudaMemcpyAsync(f + i * P + n0, c->staging + i * cnt, cnt * 8, cudaMemcpyDeviceToHost,
+                          c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "copying populations");
+  }
+  return sync(c, "get_populations");
+}
+
+lb_status lb_set_populations(lb_ctx* c, const double* f, int on_device) {
+  if (!c) return LB_ERR_INVALID_ARG;
+  if (!f) return fail(c, LB_ERR_INVALID_ARG, "f is NULL");
+  const uint64_t P = c->box.P;
+  c->gamma_valid = false;
+  cudaError_t e;
+  if (on_device) {
+    e = dispatch(c, [&](auto ops) { return ops.set(c->box, c->t, f, 0, P, P, c->stream); });
+    if (e != cudaSuccess) return cuda_fail(c, e, "import kernel");
+    return sync(c, "set_populations");
+  }
+  for (uint64_t n0 = 0; n0 < P; n0 += c->stage_nodes) {
+    const uint64_t cnt = (P - n0 < c->stage_nodes) ? P - n0 : c->stage_nodes;
+    e = cudaSuccess;
+    for (int i = 0; i < 27 && e == cudaSuccess; ++i)
+      e = cudaMemcpyAsync(c->staging + i * cnt, f + i * P + n0, cnt * 8, cudaMemcpyHostToDevice,
+                          c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "copying populations");
+    e = dispatch(c, [&](auto ops) { return ops.set(c->box, c->t, c->staging, n0, cnt, cnt, c->stream); });
+    if (e != cudaSuccess) return cuda_fail(c, e, "import kernel");
+  }
+  return sync(c, "set_populations");
+}
+
+int64_t lb_time(const lb_ctx* c) { return c ? c->t : -1; }
+double lb_beta(const lb_ctx* c) { return c ? c->box.beta : NAN; }
+
+lb_status lb_set_time(lb_ctx* c, int64_t t) {
+  if (!c) return LB_ERR_INVALID_ARG;
+  if (t < 0) return fail(c, LB_ERR_INVALID_ARG, "t must be >= 0");
+  c->t = t;
+  c->gamma_valid = false;
+  return LB_OK;
+}
+
+lb_status lb_set_block(lb_ctx* c, int32_t bx, int32_t by) {
+  if (!c) return LB_ERR_INVALID_ARG;
+  const int n = bx * by;
+  if (bx < 32 || bx % 32 != 0 || by < 1 || (n != 64 && n != 128 && n != 256 && n != 512))
+    return fail(c, LB_ERR_INVALID_ARG, "block must be bx*by in {64,128,256,512}, bx % 32 == 0");
+  if (c->cfg.storage == LB_F64 && n > 256)
+    return fail(c, LB_ERR_INVALID_ARG, "FP64 storage allows at most 256 threads per block");
+  c->bx = bx;
+  c->by = by;
+  return LB_OK;
+}
+
+}  // extern "C"
+
+// ====================================================================== batched ensemble
+
+struct lb_batch {
+  int nbox = 0;
+  lb_config base_cfg;
+  std::vector<lb_ctx*> views;
+  std::vector<lb_config> cfgs;
+  kbc::BoxDesc* d_boxes = nullptr;
+  kbc::WorkItem* d_items = nullptr;
+  size_t max_items = 0;
+  int nitems = 0;
+  int threads = 256;
+  int tile = 512;  // target nodes per work item
+  int grid = 1;
+  cudaStream_t stream = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  std::map<std::pair<int64_t, int>, cudaGraphExec_t> graphs;
+  int64_t t = 0;
+  std::string err;
+};
+
+namespace {
+
+lb_status bfail(lb_batch* b, lb_status s, const std::string& m) {
+  if (b) b->err = m;
+  return s;
+}
+
+struct BatchLayout {
+  size_t boxes, items, shared_off, total;
+  size_t max_items;
+  std::vector<BoxLayout> box;
+  SharedLayout shared;
+};
+
+bool batch_layout(const lb_config* cfgs, int32_t nbox, BatchLayout* L, std::string* why) {
+  if (!cfgs || nbox < 1) {
+    *why = "need at least one box";
+    return false;
+  }
+  uint64_t maxP = 0;
+  size_t rows = 0;
+  for (int b = 0; b < nbox; ++b) {
+    lb_config c = cfgs[b];
+    c.variant = cfgs[0].variant;
+    c.gamma_mode = cfgs[0].gamma_mode;
+    c.storage = cfgs[0].storage;
+    c.scheme = cfgs[0].scheme;
+    if (!valid_config(&c, why)) {
+      *why = "box " + std::to_string(b) + ": " + *why;
+      return false;
+    }
+    const uint64_t P = (uint64_t)c.nx * c.ny * c.nz;
+    if (P > maxP) maxP = P;
+    rows += (size_t)c.ny * c.nz;
+  }
+  size_t off = 0;
+  L->boxes = off;
+  off = align_up(off + sizeof(kbc::BoxDesc) * nbox);
+  L->items = off;
+  L->max_items = rows;
+  off = align_up(off + sizeof(kbc::WorkItem) * rows);
+  L->box.clear();
+  for (int b = 0; b < nbox; ++b) {
+    lb_config c = cfgs[b];
+    c.storage = cfgs[0].storage;
+    c.scheme = cfgs[0].scheme;
+    BoxLayout B = box_layout(&c, off);
+    L->box.push_back(B);
+    off = B.total;
+  }
+  L->shared = shared_layout(cfgs[0].storage, maxP, off);
+  L->total = L->shared.total;
+  return true;
+}
+
+void clear_graphs(lb_batch* b) {
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  b->graphs.clear();
+}
+
+int num_sms() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+// rebuild the work list for the current tile and upload it
+lb_status build_items(lb_batch* b) {
+  std::vector<kbc::WorkItem> items;
+  items.reserve(b->max_items);
+  for (int k = 0; k < b->nbox; ++k) {
+    const lb_config& c = b->cfgs[k];
+    int rows_per = b->tile / c.nx;
+    if (rows_per < 1) rows_per = 1;
+    const int rows = c.ny * c.nz;
+    for (int r = 0; r < rows; r += rows_per) {
+      kbc::WorkItem w;
+      w.box = k;
+      w.row0 = r;
+      w.nrows = (rows - r < rows_per) ? rows - r : rows_per;
+      w.pad = 0;
+      items.push_back(w);
+    }
+  }
+  b->nitems = (int)items.size();
+  cudaError_t e = cudaMemcpyAsync(b->d_items, items.data(), sizeof(kbc::WorkItem) * items.size(),
+                                  cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bfail(b, LB_ERR_CUDA, std::string("uploading work list: ") + cudaGetErrorString(e));
+  int occ = 1;
+  switch (b->base_cfg.storage) {
+    case LB_F64: occ = kbc::Ops<double>::batch_occupancy(b->threads, b->base_cfg.scheme); break;
+    case LB_F32: occ = kbc::Ops<float>::batch_occupancy(b->threads, b->base_cfg.scheme); break;
+    default: occ = kbc::Ops<uint16_t>::batch_occupancy(b->threads, b->base_cfg.scheme); break;
+  }
+  const int cap = num_sms() * occ;
+  b->grid = b->nitems < cap ? b->nitems : cap;
+  clear_graphs(b);
+  return LB_OK;
+}
+
+cudaError_t enqueue_batch_step(lb_batch* b, int64_t t, bool record, cudaStream_t st) {
+  const lb_config& c = b->base_cfg;
+  const int wt = (c.variant == LB_S_DT || c.variant == LB_S_DTQ);
+  const int wq = (c.variant == LB_S_DQ || c.variant == LB_S_DTQ);
+  switch (c.storage) {
+    case LB_F64:
+      return kbc::Ops<double>::batch_step(b->d_boxes, b->d_items, b->nitems, t, record, c.scheme,
+                                          wt, wq, c.gamma_mode, b->threads, b->grid, st);
+    case LB_F32:
+      return kbc::Ops<float>::batch_step(b->d_boxes, b->d_items, b->nitems, t, record, c.scheme,
+                                         wt, wq, c.gamma_mode, b->threads, b->grid, st);
+    default:
+      return kbc::Ops<uint16_t>::batch_step(b->d_boxes, b->d_items, b->nitems, t, record,
+                                            c.scheme, wt, wq, c.gamma_mode, b->threads, b->grid,
+                                            st);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lb_batch_required_bytes(const lb_config* cfgs, int32_t nbox) {
+  BatchLayout L;
+  std::string why;
+  if (!batch_layout(cfgs, nbox, &L, &why)) return 0;
+  return L.total;
+}
+
+lb_status lb_batch_create(const lb_config* cfgs, int32_t nbox, void* dev_buf, size_t bytes,
+                          void* stream, lb_batch** out) {
+  if (!out) {
+    g_create_error = "out is NULL";
+    return LB_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  BatchLayout L;
+  std::string why;
+  if (!batch_layout(cfgs, nbox, &L, &why)) {
+    g_create_error = why;
+    return LB_ERR_INVALID_ARG;
+  }
+  if (!dev_buf || ((uintptr_t)dev_buf % kAlign) != 0) {
+    g_create_error = "dev_buf must be a non-NULL 256-byte aligned device pointer";
+    return LB_ERR_INVALID_ARG;
+  }
+  if (bytes < L.total) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "buffer of %zu bytes is smaller than the %zu bytes required", bytes,
+             L.total);
+    g_create_error = buf;
+    return LB_ERR_OOM;
+  }
+  lb_status s = check_device(&why);
+  if (s != LB_OK) {
+    g_create_error = why;
+    return s;
+  }
+  lb_batch* b = new lb_batch();
+  char* base = (char*)dev_buf;
+  b->nbox = nbox;
+  b->base_cfg = cfgs[0];
+  b->stream = (cudaStream_t)stream;
+  b->d_boxes = (kbc::BoxDesc*)(base + L.boxes);
+  b->d_items = (kbc::WorkItem*)(base + L.items);
+  b->max_items = L.max_items;
+  cudaError_t e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("creating capture stream: ") + cudaGetErrorString(e);
+    delete b;
+    return LB_ERR_CUDA;
+  }
+  std::vector<kbc::BoxDesc> descs(nbox);
+  for (int k = 0; k < nbox; ++k) {
+    lb_config c = cfgs[k];
+    c.variant = cfgs[0].variant;
+    c.gamma_mode = cfgs[0].gamma_mode;
+    c.storage = cfgs[0].storage;
+    c.scheme = cfgs[0].scheme;
+    b->cfgs.push_back(c);
+    lb_ctx* v = new lb_ctx();
+    setup_ctx(v, &c, base, L.box[k], L.shared, b->stream);
+    v->batch_view = true;
+    s = zero_state(v);
+    b->views.push_back(v);
+    kbc::BoxDesc& d = descs[k];
+    d.nx = c.nx;
+    d.ny = c.ny;
+    d.nz = c.nz;
+    d.nxy = (uint32_t)c.nx * c.ny;
+    d.pop[0] = v->box.pop[0];
+    d.pop[1] = v->box.pop[1];
+    d.gamma = v->box.gamma;
+    d.ctr = v->counters;
+    d.beta = v->box.beta;
+    d.two_beta = 2.0 * v->box.beta;
+    d.inv_beta = 1.0 / v->box.beta;
+  }
+  e = cudaMemcpyAsync(b->d_boxes, descs.data(), sizeof(kbc::BoxDesc) * nbox,
+                      cudaMemcpyHostToDevice, b->stream);
+  if (e != cudaSuccess || s != LB_OK) {
+    g_create_error = "initialising batch: " + std::string(cudaGetErrorString(e));
+    lb_batch_destroy(b);
+    return LB_ERR_CUDA;
+  }
+  s = build_items(b);
+  if (s != LB_OK) {
+    g_create_error = b->err;
+    lb_batch_destroy(b);
+    return s;
+  }
+  *out = b;
+  return LB_OK;
+}
+
+lb_status lb_batch_destroy(lb_batch* b) {
+  if (!b) return LB_ERR_INVALID_ARG;
+  clear_graphs(b);
+  for (lb_ctx* v : b->views) delete v;
+  if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+  delete b;
+  return LB_OK;
+}
+
+const char* lb_batch_last_error(const lb_batch* b) {
+  return b ? b->err.c_str() : g_create_error.c_str();
+}
+
+lb_ctx* lb_batch_box(lb_batch* b, int32_t box) {
+  if (!b || box < 0 || box >= b->nbox) return nullptr;
+  return b->views[box];
+}
+
+lb_status lb_batch_step(lb_batch* b, int64_t n) {
+  if (!b) return LB_ERR_INVALID_ARG;
+  if (n < 0) return bfail(b, LB_ERR_INVALID_ARG, "n must be >= 0");
+  if (n == 0) return LB_OK;
+  for (lb_ctx* v : b->views)
+    if (v->t != b->t)
+      return bfail(b, LB_ERR_INVALID_ARG, "a box was stepped or re-timed on its own; all boxes "
+                                          "of a batch must share the time t");
+  const auto key = std::make_pair(n, (int)(b->t & 1));
+  auto it = b->graphs.find(key);
+  if (it == b->graphs.end()) {
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess)
+      return bfail(b, LB_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+    cudaError_t le = cudaSuccess;
+    for (int64_t k = 0; k < n; ++k) {
+      const bool record = (k == n - 1);
+      if (record) {
+        for (lb_ctx* v : b->views)
+          if (le == cudaSuccess)
+            le = cudaMemsetAsync(v->counters, 0, sizeof(kbc::StepCounters), b->capture_stream);
+      }
+      if (le == cudaSuccess) le = enqueue_batch_step(b, b->t + k, record, b->capture_stream);
+    }
+    e = cudaStreamEndCapture(b->capture_stream, &graph);
+    if (le != cudaSuccess || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return bfail(b, LB_ERR_CUDA, std::string("capturing batch steps: ") +
+                                       cudaGetErrorString(le != cudaSuccess ? le : e));
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess)
+      return bfail(b, LB_ERR_CUDA, std::string("instantiating graph: ") + cudaGetErrorString(e));
+    it = b->graphs.emplace(key, exec).first;
+  }
+  cudaError_t e = cudaGraphLaunch(it->second, b->stream);
+  if (e != cudaSuccess)
+    return bfail(b, LB_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+  b->t += n;
+  for (lb_ctx* v : b->views) {
+    v->t = b->t;
+    v->gamma_valid = true;
+  }
+  return LB_OK;
+}
+
+lb_status lb_batch_diagnostics(lb_batch* b, lb_diag* out) {
+  if (!b || !out) return b ? bfail(b, LB_ERR_INVALID_ARG, "out is NULL") : LB_ERR_INVALID_ARG;
+  lb_status worst = LB_OK;
+  for (int k = 0; k < b->nbox; ++k) {
+    lb_status s = lb_diagnostics(b->views[k], &out[k]);
+    if (s == LB_ERR_NONFINITE) {
+      worst = s;
+      b->err = "box " + std::to_string(k) + ": " + b->views[k]->err;
+    } else if (s != LB_OK) {
+      b->err = "box " + std::to_string(k) + ": " + b->views[k]->err;
+      return s;
+    }
+  }
+  return worst;
+}
+
+lb_status lb_batch_set_tile(lb_batch* b, int32_t threads, int32_t tile) {
+  if (!b) return LB_ERR_INVALID_ARG;
+  const int maxt = b->base_cfg.storage == LB_F64 ? 256 : 512;
+  if (threads < 32 || threads > maxt || threads % 32 != 0 || tile < 32)
+    return bfail(b, LB_ERR_INVALID_ARG, "threads must be a multiple of 32 in [32, 512] (256 for "
+                                        "FP64); tile >= 32");
+  b->threads = threads;
+  b->tile = tile;
+  return build_items(b);
+}
+
+lb_status lb_batch_autotune(lb_batch* b, int32_t trial_steps, int32_t* best_threads,
+                            int32_t* best_tile, double* best_ms) {
+  if (!b) return LB_ERR_INVALID_ARG;
+  if (trial_steps < 1) return bfail(b, LB_ERR_INVALID_ARG, "trial_steps must be >= 1");
+  const int cand_threads[] = {128, 256, 512};
+  const int maxt = b->base_cfg.storage == LB_F64 ? 256 : 512;
+  const int cand_tile[] = {256, 512, 1024, 2048, 4096};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return bfail(b, LB_ERR_CUDA, "creating timing events");
+  double best = 1e300;
+  int bt = b->threads, bl = b->tile;
+  lb_status st = LB_OK;
+  for (int th : cand_threads) {
+    if (th > maxt) continue;
+    for (int tl : cand_tile) {
+      b->threads = th;
+      b->tile = tl;
+      st = build_items(b);
+      if (st != LB_OK) break;
+      cudaError_t e = enqueue_batch_step(b, b->t, false, b->stream);  // warm-up
+      b->t += 1;
+      if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+      for (int k = 0; k < trial_steps && e == cudaSuccess; ++k) {
+        e = enqueue_batch_step(b, b->t, false, b->stream);
+        b->t += 1;
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        st = bfail(b, LB_ERR_CUDA, std::string("autotune trial: ") + cudaGetErrorString(e));
+        break;
+      }
+      const double per = ms / trial_steps;
+      if (per < best) {
+        best = per;
+        bt = th;
+        bl = tl;
+      }
+    }
+    if (st != LB_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (lb_ctx* v : b->views) {
+    v->t = b->t;
+    v->gamma_valid = false;
+  }
+  if (st != LB_OK) return st;
+  b->threads = bt;
+  b->tile = bl;
+  st = build_items(b);
+  if (st != LB_OK) return st;
+  if (best_threads) *best_threads = bt;
+  if (best_tile) *best_tile = bl;
+  if (best_ms) *best_ms = best;
+  return LB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,83 @@
+"""The C ABI library builds, loads, exports every symbol the header declares, and its host-side
+validation works without a GPU (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "kbc_lb.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(lb_[a-z_]+)\s*\(",
+                       text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1507_02518_gb300 import build, lb
+    build.build()
+    return lb.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("lb_create", "lb_init_field", "lb_step", "lb_moments", "lb_diagnostics",
+                 "lb_get_populations", "lb_set_populations", "lb_batch_step"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_1507_02518_gb300 import lb
+    names = declared_functions()
+    for n in names:
+        assert hasattr(lib, n), "libkbc.so does not export %s" % n
+    assert sorted(lb.SYMBOLS) == names
+
+
+def test_required_bytes_and_validation(lib):
+    from paper_1507_02518_gb300 import lb
+    c = lb.make_config(32, storage="f64", scheme="pull")
+    need_pull = lb.lb_required_bytes(c)
+    assert need_pull >= 2 * 27 * 32 ** 3 * 8
+    c_aa = lb.make_config(32, storage="f64", scheme="aa")
+    assert lb.lb_required_bytes(c_aa) < need_pull
+    assert lb.lb_required_bytes(lb.make_config(32, storage="f16")) < lb.lb_required_bytes(
+        lb.make_config(32, storage="f32"))
+    for bad in (lb.make_config(2), lb.make_config(32, nu=0.0), lb.make_config(32, nu=-1.0),
+                lb.make_config(1 << 11, 1 << 10, 1 << 10)):
+        assert lb.lb_required_bytes(bad) == 0
+    c_bad = lb.make_config(32)
+    c_bad.variant = 9
+    assert lb.lb_required_bytes(c_bad) == 0
+
+
+def test_create_rejects_bad_arguments_on_host(lib):
+    from paper_1507_02518_gb300 import lb
+    with pytest.raises(lb.LBError) as e:
+        lb.lb_create(lb.make_config(2), 256, 1 << 30, 0)
+    assert e.value.status == lb.LB_ERR_INVALID_ARG
+    with pytest.raises(lb.LBError) as e:
+        lb.lb_create(lb.make_config(32), 256, 100, 0)
+    assert e.value.status == lb.LB_ERR_OOM
+    with pytest.raises(lb.LBError) as e:
+        lb.lb_create(lb.make_config(32), 0, 1 << 30, 0)
+    assert e.value.status == lb.LB_ERR_INVALID_ARG
+    with pytest.raises(lb.LBError) as e:
+        lb.lb_create(lb.make_config(32), 100, 1 << 30, 0)   # misaligned
+    assert e.value.status == lb.LB_ERR_INVALID_ARG
+    with pytest.raises(lb.LBError) as e:
+        lb.lb_batch_create([], 256, 1 << 30, 0)
+    assert e.value.status == lb.LB_ERR_INVALID_ARG
+
+
+def test_null_handles_are_rejected(lib):
+    assert lib.lb_step(None, 1) == 1
+    assert lib.lb_destroy(None) == 1
+    assert lib.lb_batch_step(None, 1) == 1
+    assert lib.lb_time(None) == -1

@@ -1,0 +1,396 @@
+"""GPU (CUDA, through the C ABI) against the FP64 CPU oracle on the same seeded inputs.
+
+Tolerances:
+  * FP64 storage: max |df| <= 1e-12 after 100 steps (the stated FP64 bar).
+  * FP32 storage, one step from identical stored inputs: every population within
+    FP32_STEP_TOL (derived from FP32 round-off of the collision) of the oracle.
+  * FP16 storage, one step: the stored half of (f - W)/W equals the oracle's result rounded
+    to half, or is one half-ulp away (the two sides round values that differ by FP32 error).
+  * Index/layout work (set/get round trips, pull vs AA, batch vs single box, checkpoints):
+    bit-exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1507_02518_gb300 import lb, workloads
+
+pytestmark = pytest.mark.gpu
+
+V, W = oracle.lattice()
+W4 = W.reshape(27, 1, 1, 1)
+FP64_TOL = 1e-12
+FP32_STEP_TOL = 2e-7
+
+
+def seeded_state(nx, ny, nz, seed=3, u0=0.05, noise=1e-4):
+    """Taylor-Green-like velocity on any box, plus multiplicative noise 1e-4 on populations."""
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    kx, ky, kz = 2 * math.pi / nx, 2 * math.pi / ny, 2 * math.pi / nz
+    u = np.zeros((3, nz, ny, nx))
+    u[0] = u0 * np.sin(kx * x) * np.cos(ky * y) * np.cos(kz * z)
+    u[1] = -u0 * np.cos(kx * x) * np.sin(ky * y) * np.cos(kz * z)
+    u[2] = 0.3 * u0 * np.sin(kz * z) * np.cos(kx * x)
+    rho = 1.0 + 0.01 * np.cos(kx * x + ky * y)
+    f = oracle.init_equilibrium(rho, u)
+    return f * (1.0 + noise * workloads.population_noise(nx, ny, nz, seed))
+
+
+def lattice(shape, **kw):
+    nx, ny, nz = shape
+    return lb.Lattice(nx, ny, nz, **kw)
+
+
+# ------------------------------------------------------------------ layout and transfer
+
+@pytest.mark.parametrize("scheme", ["pull", "aa"])
+@pytest.mark.parametrize("t", [0, 1, 4, 7])
+def test_set_get_roundtrip_is_exact_fp64(kbc, scheme, t):
+    f = seeded_state(5, 7, 9)
+    lat = lattice((5, 7, 9), storage="f64", scheme=scheme)
+    lb.lb_set_time(lat.ctx, t)
+    lat.set_populations(f)
+    g = lat.get_populations()
+    # stored as f - W in FP64: the round trip may move the last bit of f only
+    assert np.max(np.abs(g - f)) <= 1.2e-16
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_set_get_rounds_to_storage(kbc, storage):
+    f = seeded_state(6, 5, 4)
+    lat = lattice((6, 5, 4), storage=storage, scheme="aa")
+    lat.set_populations(f)
+    g = lat.get_populations()
+    if storage == "f32":
+        expect = W4 + (f - W4).astype(np.float32).astype(np.float64)
+    else:
+        expect = W4 + W4 * ((f - W4) / W4).astype(np.float16).astype(np.float64)
+    assert np.max(np.abs(g - expect)) <= 1e-16
+
+
+@pytest.mark.parametrize("scheme", ["pull", "aa"])
+def test_init_field_matches_oracle_equilibrium(kbc, scheme):
+    import torch
+    rho, u = workloads.kida(12, 0.05)
+    rho = rho * (1.0 + 0.02 * np.sin(np.arange(12))[None, None, :])
+    ref = oracle.init_equilibrium(rho, u)
+    lat = lattice((12, 12, 12), storage="f64", scheme=scheme)
+    lat.init_field(rho, u)                                     # host path
+    assert lat.t == 0
+    assert np.max(np.abs(lat.get_populations() - ref)) <= 2e-16
+    lat.init_field(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())   # device path
+    assert np.max(np.abs(lat.get_populations() - ref)) <= 2e-16
+
+
+def test_zero_steps_is_identity(kbc):
+    f = seeded_state(8, 8, 8)
+    lat = lattice((8, 8, 8), storage="f64", scheme="aa")
+    lat.set_populations(f)
+    lat.step(0)
+    assert lat.t == 0
+    assert np.array_equal(lat.get_populations(), lat.get_populations())
+    with pytest.raises(lb.LBError):
+        lat.step(-1)
+
+
+# ------------------------------------------------------------------ FP64 parity
+
+@pytest.mark.parametrize("scheme", ["pull", "aa"])
+def test_fp64_matches_oracle_100_steps_32cubed(kbc, scheme):
+    """32^3 Taylor-Green + seeded noise, nu = 1e-3: max |df| <= 1e-12 after 100 steps."""
+    n, nu, steps = 32, 1e-3, 100
+    rho, u = workloads.taylor_green(n, 0.05)
+    f0 = oracle.init_equilibrium(rho, u) * (1 + 1e-4 * workloads.population_noise(n, n, n, 11))
+    lat = lattice((n, n, n), nu=nu, storage="f64", scheme=scheme)
+    lat.set_populations(f0)
+    lat.step(steps)
+    ref, _, _ = oracle.run(f0, steps, oracle.beta(nu))
+    err = np.max(np.abs(lat.get_populations() - ref))
+    assert err <= FP64_TOL, err
+
+
+@pytest.mark.parametrize("shape", [(3, 3, 3), (5, 7, 9), (40, 6, 3), (33, 17, 5)])
+@pytest.mark.parametrize("scheme", ["pull", "aa"])
+def test_fp64_matches_oracle_ragged_boxes(kbc, shape, scheme):
+    f0 = seeded_state(*shape)
+    steps = 9
+    lat = lattice(shape, nu=2e-3, storage="f64", scheme=scheme)
+    lat.set_populations(f0)
+    lat.step(steps)
+    ref, _, _ = oracle.run(f0, steps, oracle.beta(2e-3))
+    assert np.max(np.abs(lat.get_populations() - ref)) <= FP64_TOL
+
+
+@pytest.mark.parametrize("variant", ["d", "d+t", "d+q", "d+t+q"])
+@pytest.mark.parametrize("gamma", ["estimate", "lbgk", "rlb"])
+def test_fp64_matches_oracle_variants(kbc, variant, gamma):
+    f0 = seeded_state(10, 9, 8, noise=1e-3)
+    steps = 6
+    nu = 5e-4
+    lat = lattice((10, 9, 8), nu=nu, storage="f64", scheme="aa", variant=variant, gamma=gamma)
+    lat.set_populations(f0)
+    lat.step(steps)
+    ref, _, _ = oracle.run(f0, steps, oracle.beta(nu), lb.VARIANT[variant], lb.GAMMA[gamma])
+    assert np.max(np.abs(lat.get_populations() - ref)) <= FP64_TOL
+
+
+@pytest.mark.parametrize("bx,by", [(32, 2), (64, 1), (32, 8), (128, 2)])
+def test_fp64_launch_shapes_agree(kbc, bx, by):
+    f0 = seeded_state(37, 11, 5)
+    lat = lattice((37, 11, 5), storage="f64", scheme="pull")
+    lat.set_block(bx, by)
+    lat.set_populations(f0)
+    lat.step(3)
+    ref, _, _ = oracle.run(f0, 3, oracle.beta(1e-3))
+    assert np.max(np.abs(lat.get_populations() - ref)) <= FP64_TOL
+
+
+# ------------------------------------------------------------------ cross-scheme, determinism
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("steps", [7, 8])
+def test_pull_and_aa_are_bitwise_identical(kbc, storage, steps):
+    f0 = seeded_state(20, 12, 9)
+    out = []
+    for scheme in ("pull", "aa"):
+        lat = lattice((20, 12, 9), storage=storage, scheme=scheme)
+        lat.set_populations(f0)
+        lat.step(steps)
+        out.append(lat.get_populations())
+    assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("scheme", ["pull", "aa"])
+def test_checkpoint_resume_is_bitwise(kbc, scheme, tmp_path):
+    f0 = seeded_state(16, 8, 6)
+    a = lattice((16, 8, 6), storage="f32", scheme=scheme)
+    a.set_populations(f0)
+    a.step(11)
+    ref = a.get_populations()
+    b = lattice((16, 8, 6), storage="f32", scheme=scheme)
+    b.set_populations(f0)
+    b.step(5)
+    path = str(tmp_path / "ck.bin")
+    b.save_checkpoint(path)
+    c = lattice((16, 8, 6), storage="f32", scheme=scheme)
+    c.load_checkpoint(path)
+    assert c.t == 5
+    c.step(6)
+    assert np.array_equal(c.get_populations(), ref)
+    # a truncated checkpoint is rejected
+    with open(path, "rb") as fh:
+        data = fh.read()
+    with open(path, "wb") as fh:
+        fh.write(data[:-8])
+    with pytest.raises(lb.LBError):
+        c.load_checkpoint(path)
+
+
+# ------------------------------------------------------------------ FP32 / FP16 parity
+
+def one_step_reference(lat, steps_before=0):
+    """Oracle step from exactly the state the GPU holds (decoded from its storage)."""
+    f_in = lat.get_populations()
+    ref, _, _ = oracle.run(f_in, 1, lat.beta)
+    lat.step(1)
+    return lat.get_populations(), ref, f_in
+
+
+@pytest.mark.parametrize("scheme", ["pull", "aa"])
+def test_fp32_one_step_parity(kbc, scheme):
+    n = 24
+    rho, u = workloads.random_spectrum(n, 4, 0.04, seed=1)
+    f0 = oracle.init_equilibrium(rho, u) * (1 + 1e-4 * workloads.population_noise(n, n, n, 5))
+    lat = lattice((n, n, n), nu=2e-4, storage="f32", scheme=scheme)
+    lat.set_populations(f0)
+    lat.step(3)                      # odd number: AA is in its swapped layout
+    got, ref, _ = one_step_reference(lat)
+    err = np.max(np.abs(got - ref))
+    assert err <= FP32_STEP_TOL, err
+
+
+@pytest.mark.parametrize("scheme", ["pull", "aa"])
+def test_fp16_one_step_parity_within_one_half_ulp(kbc, scheme):
+    n = 24
+    rho, u = workloads.random_spectrum(n, 4, 0.04, seed=2)
+    f0 = oracle.init_equilibrium(rho, u) * (1 + 1e-4 * workloads.population_noise(n, n, n, 6))
+    lat = lattice((n, n, n), nu=2e-4, storage="f16", scheme=scheme)
+    lat.set_populations(f0)
+    lat.step(2)
+    got, ref, _ = one_step_reference(lat)
+    h_got = ((got - W4) / W4).astype(np.float16)
+    h_ref = ((ref - W4) / W4).astype(np.float16)
+    # got is exactly representable; compare in units of the half ulp at each value
+    ulp = np.spacing(np.abs(h_ref).astype(np.float16)).astype(np.float64)
+    diff = np.abs(h_got.astype(np.float64) - h_ref.astype(np.float64))
+    assert np.all(diff <= ulp * 1.0001), float(np.max(diff / ulp))
+    assert np.mean(h_got == h_ref) > 0.99
+
+
+def test_fp32_and_fp16_trajectory_error_vs_fp64(kbc):
+    """Stated error of the reduced-precision storage after 100 steps on a 24^3 random field."""
+    n, nu, steps = 24, 2e-4, 100
+    rho, u = workloads.random_spectrum(n, 4, 0.04, seed=3)
+    f0 = oracle.init_equilibrium(rho, u)
+    ref, _, _ = oracle.run(f0, steps, oracle.beta(nu))
+    errs = {}
+    for storage in ("f32", "f16"):
+        lat = lattice((n, n, n), nu=nu, storage=storage, scheme="aa")
+        lat.init_field(rho, u)
+        lat.step(steps)
+        errs[storage] = float(np.max(np.abs(lat.get_populations() - ref)))
+    assert errs["f32"] <= 2e-6, errs
+    assert errs["f16"] <= 2e-4, errs
+
+
+# ------------------------------------------------------------------ moments and diagnostics
+
+@pytest.mark.parametrize("scheme", ["pull", "aa"])
+def test_moments_and_diagnostics_match_oracle(kbc, scheme):
+    n, nu = 16, 1e-3
+    rho, u = workloads.kida(n, 0.05)
+    f0 = oracle.init_equilibrium(rho, u)
+    lat = lattice((n, n, n), nu=nu, storage="f64", scheme=scheme)
+    lat.set_populations(f0)
+    lat.step(4)
+    f_prev = lat.get_populations()
+    lat.step(1)
+    f = lat.get_populations()
+    r_ref, u_ref = oracle.macroscopic(f)
+    r_gpu, u_gpu = lat.moments()
+    assert np.max(np.abs(r_gpu - r_ref)) <= 1e-14
+    assert np.max(np.abs(u_gpu - u_ref)) <= 1e-14
+    d = lat.diagnostics()
+    dref = oracle.diagnostics(r_ref, u_ref, nu)
+    assert d["step"] == 5 and d["nodes"] == n ** 3
+    assert d["mass"] == pytest.approx(dref["mass"], rel=1e-13)
+    assert np.allclose(d["momentum"], dref["momentum"], atol=1e-12)
+    for key in ("kinetic_energy", "enstrophy", "dissipation"):
+        assert d[key] == pytest.approx(dref[key], rel=1e-10), key
+    # gamma statistics of the collision that produced f (recorded in FP32 per node)
+    _, g_ref, guarded = oracle.collide_field(f_prev, lat.beta, want_gamma=True)
+    assert d["gamma_mean"] == pytest.approx(float(np.mean(g_ref)), rel=1e-6)
+    assert d["gamma_std"] == pytest.approx(float(np.std(g_ref)), rel=1e-4, abs=1e-7)
+    assert d["den_guard_count"] == guarded
+    assert d["nonfinite_count"] == 0
+
+
+def test_rest_state_is_exact_and_guarded(kbc):
+    lat = lattice((8, 6, 4), storage="f32", scheme="pull")
+    lat.step(3)
+    f = lat.get_populations()
+    assert np.array_equal(f, np.broadcast_to(W4, f.shape))
+    d = lat.diagnostics()
+    assert d["den_guard_count"] == 8 * 6 * 4 and d["gamma_mean"] == 2.0
+
+
+def test_nonfinite_is_reported(kbc):
+    f = seeded_state(6, 6, 6)
+    f[3, 2, 2, 2] = np.nan
+    lat = lattice((6, 6, 6), storage="f32", scheme="aa")
+    lat.set_populations(f)
+    lat.step(2)
+    with pytest.raises(lb.LBError) as e:
+        lat.diagnostics()
+    assert e.value.status == lb.LB_ERR_NONFINITE
+    d = lat.diagnostics(raise_nonfinite=False)
+    assert d["nonfinite_count"] > 0
+
+
+# ------------------------------------------------------------------ batched ensemble
+
+@pytest.mark.parametrize("storage,scheme", [("f32", "pull"), ("f32", "aa"), ("f64", "pull"),
+                                            ("f16", "aa")])
+def test_batch_matches_single_boxes_bitwise(kbc, storage, scheme):
+    boxes = [{"n": 12, "nu": 1e-3}, {"n": 9, "ny": 14, "nz": 5, "nu": 3e-4},
+             {"n": 33, "ny": 4, "nz": 6, "nu": 2e-5}]
+    batch = lb.Batch(boxes, storage=storage, scheme=scheme)
+    states = []
+    for k, b in enumerate(boxes):
+        nx, ny, nz = b["n"], b.get("ny", b["n"]), b.get("nz", b["n"])
+        f0 = seeded_state(nx, ny, nz, seed=20 + k)
+        states.append(f0)
+        view = batch.box(k)
+        ff = np.ascontiguousarray(f0)
+        lb.lb_set_populations(view, ff.ctypes.data, False)
+    batch.set_tile(128, 64)
+    batch.step(5)
+    batch.step(2)
+    for k, b in enumerate(boxes):
+        nx, ny, nz = b["n"], b.get("ny", b["n"]), b.get("nz", b["n"])
+        single = lb.Lattice(nx, ny, nz, nu=b["nu"], storage=storage, scheme=scheme)
+        single.set_populations(states[k])
+        single.step(7)
+        got = np.empty((27, nz, ny, nx))
+        lb.lb_get_populations(batch.box(k), got.ctypes.data, False)
+        assert np.array_equal(got, single.get_populations()), k
+    diags = batch.diagnostics()
+    assert len(diags) == 3 and all(d["step"] == 7 for d in diags)
+
+
+def test_batch_autotune_and_graph_replay(kbc):
+    boxes = [{"n": 16, "nu": 1e-3}, {"n": 24, "nu": 1e-4}]
+    batch = lb.Batch(boxes, storage="f32", scheme="pull")
+    th, tile, ms = batch.autotune(2)
+    assert th in (128, 256, 512) and tile >= 256 and ms > 0
+    rho, u = workloads.taylor_green(16, 0.03)
+    lb.lb_init_field(batch.box(0), rho.ctypes.data, np.ascontiguousarray(u).ctypes.data, False)
+    rho2, u2 = workloads.taylor_green(24, 0.03)
+    lb.lb_init_field(batch.box(1), rho2.ctypes.data, np.ascontiguousarray(u2).ctypes.data, False)
+    for _ in range(3):
+        batch.step(4)            # the same graph replays
+    ref = lb.Lattice(16, nu=1e-3, storage="f32", scheme="pull")
+    ref.init_field(rho, u)
+    ref.step(12)
+    got = np.empty((27, 16, 16, 16))
+    lb.lb_get_populations(batch.box(0), got.ctypes.data, False)
+    assert np.array_equal(got, ref.get_populations())
+
+
+# ------------------------------------------------------------------ full-size sampled parity
+
+def _sampled_step_check(lat, nsample, tol, rng):
+    """Compare f(t+1) at sampled nodes with the oracle applied to the GPU's f(t) (FP64 copy)."""
+    import torch
+    nz, ny, nx = lat.shape
+    P = lat.P
+    dev = torch.empty((27, P), dtype=torch.float64, device="cuda")
+    lb.lb_get_populations(lat.ctx, dev.data_ptr(), True)
+    idx = rng.integers(0, P, nsample)
+    zs, ys, xs = idx // (nx * ny), (idx // nx) % ny, idx % nx
+    # the 27 neighbours x - v_i whose post-collision values stream into each sample
+    nbr_nodes = []
+    for i in range(27):
+        vx, vy, vz = V[i]
+        nbr_nodes.append(((zs - vz) % nz) * nx * ny + ((ys - vy) % ny) * nx + (xs - vx) % nx)
+    nbr = np.stack(nbr_nodes)                             # [27 (direction), nsample]
+    cols = torch.from_numpy(nbr.reshape(-1)).cuda()
+    fin = dev[:, cols].cpu().numpy().reshape(27, 27, nsample)   # [pop, dir, sample]
+    lat.step(1)
+    lb.lb_get_populations(lat.ctx, dev.data_ptr(), True)
+    fout = dev[:, torch.from_numpy(idx).cuda()].cpu().numpy()   # [pop, sample]
+    beta = lat.beta
+    worst = 0.0
+    for s in range(nsample):
+        for i in range(27):
+            post, _, _ = oracle.collide(fin[:, i, s], beta)
+            worst = max(worst, abs(post[i] - fout[i, s]))
+    assert worst <= tol, worst
+    return worst
+
+
+def test_full_size_256cubed_fp32_sampled_parity(kbc):
+    """The benchmark configuration (256^3 random spectrum, FP32, pull): sampled one-step parity
+    and mass conservation over 10 steps."""
+    n, nu = 256, 2e-4
+    rho, u = workloads.random_spectrum(n, 4, 0.04, seed=1)
+    lat = lb.Lattice(n, nu=nu, storage="f32", scheme="pull")
+    lat.init_field(rho, u)
+    d0 = lat.diagnostics()
+    lat.step(10)
+    d1 = lat.diagnostics()
+    assert abs(d1["mass"] - d0["mass"]) / d0["mass"] < 1e-7
+    rng = np.random.default_rng(0)
+    _sampled_step_check(lat, 48, FP32_STEP_TOL, rng)
