@@ -54,6 +54,25 @@ VARIANTS = [
 NCU_TRAFFIC_PER_LUP = {}
 
 
+def parse_workload(name):
+    """hit<N>_<storage>_<scheme> (random spectrum, k0=4, u_rms=0.04, nu=2e-4) or
+    kida<N>_<storage>_<scheme> (U0=0.05, nu=5e-5), e.g. hit128_f32_pull."""
+    for v in [MAIN] + VARIANTS:
+        if v["name"] == name:
+            return dict(v)
+    import re
+    m = re.fullmatch(r"(hit|kida)(\d+)_(f64|f32|f16)_(pull|aa)", name)
+    if not m:
+        raise SystemExit("unknown workload %r" % name)
+    fam, n, storage, scheme = m.group(1), int(m.group(2)), m.group(3), m.group(4)
+    w = {"name": name, "n": n, "storage": storage, "scheme": scheme, "diag_every": 50}
+    if fam == "hit":
+        w.update(field="spectrum", k0=4.0, urms=0.04, nu=2e-4, seed=1)
+    else:
+        w.update(field="kida", U0=0.05, nu=5e-5)
+    return w
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1507_02518_gb300", "csrc")
@@ -323,6 +342,18 @@ def cpu_baseline(w, budget_s=12.0):
                       % (steps, n, dt)}
 
 
+def workload_text(w):
+    if w["field"] == "spectrum":
+        fld = ("decaying HIT, seeded random solenoidal field E(k)~k^4 exp(-2(k/k0)^2), k0=%g, "
+               "u_rms=%g, rho0=1, nu=%g" % (w["k0"], w["urms"], w["nu"]))
+    else:
+        fld = "Kida vortex U0=%g, rho0=1, nu=%g" % (w["U0"], w["nu"])
+    st = {"f64": "FP64 storage + FP64 collision", "f32": "FP32 (f-W) storage + FP32 collision",
+          "f16": "FP16 (f-W)/W storage + FP32 collision"}[w["storage"]]
+    return "%s: periodic %d^3 %s, KBC s=d+t+q, %s, %s streaming, diagnostics every %s steps" % (
+        w["name"], w["n"], fld, st, w["scheme"], w.get("diag_every"))
+
+
 def roofline(storage, mlups, peak, peak_kind, traffic=None):
     bpl = BYTES_PER_LUP[storage]
     achieved = bpl * mlups * 1e6 / 1e9
@@ -338,7 +369,7 @@ def main_ours(args, rank, world, local):
     torch.cuda.set_device(local)
     from paper_1507_02518_gb300 import lb
     lb.load()
-    w = dict(MAIN)
+    w = parse_workload(args.workload)
     peak, peak_kind = hbm_peak()
     # warm-up and timed region (max over ranks)
     barrier(world)
@@ -354,9 +385,13 @@ def main_ours(args, rank, world, local):
     kernel_mlups = res["P"] / (kernel_ms / 1e3) / 1e6
     h = kernel_source_hash()
     traffic = NCU_TRAFFIC_PER_LUP.get(h)
-    rl = roofline("f32", kernel_mlups, peak, peak_kind,
+    if w["name"] != MAIN["name"]:
+        traffic = None
+    rl = roofline(w["storage"], kernel_mlups, peak, peak_kind,
                   None if traffic is None else traffic * res["P"])
-    rl["kernel"] = "kbc::step_kernel<float, MODE_PULL>"
+    rl["kernel"] = "kbc::step_kernel<%s, %s>" % (
+        {"f64": "double", "f32": "float", "f16": "half"}[w["storage"]],
+        "MODE_PULL" if w["scheme"] == "pull" else "MODE_AA_EVEN/ODD")
     rl["kernel_ms"] = round(kernel_ms, 5)
     del res["lat"]
     torch.cuda.empty_cache()
@@ -397,16 +432,13 @@ def main_ours(args, rank, world, local):
         out = {
             "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 5),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": "hit256_f32_pull: periodic 256^3 decaying HIT, seeded random "
-                                   "solenoidal field E(k)~k^4 exp(-2(k/k0)^2), k0=4, u_rms=0.04, "
-                                   "rho0=1, nu=2e-4, KBC s=d+t+q, FP32 (f-W) storage + FP32 "
-                                   "collision, pull streaming, diagnostics every 50 steps",
-                       "box": [256, 256, 256], "storage": "f32", "scheme": "pull",
-                       "variant": "d+t+q", "diag_every": 50,
-                       "l2": "working set %.1f GB per step >> 129 MB L2 (no flush needed)"
-                             % (2 * 27 * 4 * res["P"] / 1e9),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": w["storage"], "data": "synthetic",
+            "config": {"workload": workload_text(w),
+                       "box": [w["n"]] * 3, "storage": w["storage"], "scheme": w["scheme"],
+                       "variant": "d+t+q", "diag_every": w.get("diag_every"),
+                       "l2": "populations %.2f GB read+written per step vs 129 MB L2 (no flush)"
+                             % (BYTES_PER_LUP[w["storage"]] * res["P"] / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": rl, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": res["launches"],
@@ -464,6 +496,8 @@ def parse_args(argv=None):
     p.add_argument("--steps", type=int, default=None)
     p.add_argument("--warmup", type=int, default=None)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default=MAIN["name"],
+                   help="hit<N>_<f64|f32|f16>_<pull|aa> or kida<N>_..., default %s" % MAIN["name"])
     p.add_argument("--no-variants", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")

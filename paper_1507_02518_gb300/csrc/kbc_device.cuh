@@ -78,22 +78,6 @@ template <> struct Codec<uint16_t> {
   }
 };
 
-// ------------------------------------------------------------------ numeric helpers
-template <typename R> __device__ __forceinline__ R rsq(R x);
-template <> __device__ __forceinline__ float rsq<float>(float x) { return sqrtf(x); }
-template <> __device__ __forceinline__ double rsq<double>(double x) { return sqrt(x); }
-
-// three reciprocals with one division: 1/p0 = p1 p2 / (p0 p1 p2), ...
-template <typename R>
-__device__ __forceinline__ void recip3(R p0, R p1, R p2, R& r0, R& r1, R& r2) {
-  const R p12 = p1 * p2;
-  const R q = R(1) / (p0 * p12);
-  r0 = p12 * q;
-  const R qp0 = q * p0;
-  r1 = p2 * qp0;
-  r2 = p1 * qp0;
-}
-
 // guard on <dh|dh> (the paper is silent when it vanishes; gamma falls back to 2, LBGK)
 template <typename R> struct Guard;
 template <> struct Guard<double> { static constexpr double den = 1e-300; };
@@ -110,28 +94,54 @@ struct CollideParams {
   int gamma_mode;   // GAMMA_*
 };
 
+// Explicitly rounded arithmetic. Every operation of the collision goes through these, so
+// the compiler neither contracts nor reorders anything: all kernels that inline collide()
+// (pull, AA even/odd, batched) produce bit-identical populations from identical inputs.
+template <typename R> struct Ar;
+template <> struct Ar<float> {
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float fma(float a, float b, float c) {
+    return __fmaf_rn(a, b, c);
+  }
+  static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+  static __device__ __forceinline__ float sqrt(float a) { return __fsqrt_rn(a); }
+};
+template <> struct Ar<double> {
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double fma(double a, double b, double c) {
+    return __fma_rn(a, b, c);
+  }
+  static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+  static __device__ __forceinline__ double sqrt(double a) { return __dsqrt_rn(a); }
+};
+
 // One KBC collision on the shifted populations d[i] = f_i - W_i, in place (collision
 // listing of Sec. KBC). Returns gamma; *guarded is set when <dh|dh> fell under the guard.
 template <typename R>
 __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, bool* guarded) {
+  using O = Ar<R>;
   // ---- natural moments of delta by a factorised x -> y -> z reduction (eq:natmoments)
   // row r = (vy+1) + 3(vz+1); X0 = sum over vx, X1 = sum vx, X2 = sum vx^2
   R X0[9], X1[9], X2[9];
 #pragma unroll
   for (int r = 0; r < 9; ++r) {
     const R m = d[3 * r + 0], z = d[3 * r + 1], p = d[3 * r + 2];
-    X2[r] = p + m;
-    X1[r] = p - m;
-    X0[r] = X2[r] + z;
+    X2[r] = O::add(p, m);
+    X1[r] = O::sub(p, m);
+    X0[r] = O::add(X2[r], z);
   }
   // y stage: Yp_q[c] = sum over vy of Xp * vy^q, c = vz+1
   auto ystage = [](const R (&X)[9], R (&Y0)[3], R (&Y1)[3], R (&Y2)[3]) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const R m = X[3 * c + 0], z = X[3 * c + 1], p = X[3 * c + 2];
-      Y2[c] = p + m;
-      Y1[c] = p - m;
-      Y0[c] = Y2[c] + z;
+      Y2[c] = O::add(p, m);
+      Y1[c] = O::sub(p, m);
+      Y0[c] = O::add(Y2[c], z);
     }
   };
   R Y00[3], Y01[3], Y02[3], Y10[3], Y11[3], Y12[3], Y20[3], Y21[3], Y22[3];
@@ -140,88 +150,117 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, bool* 
   ystage(X2, Y20, Y21, Y22);
   (void)Y22;
   // z stage: D_pqr = sum over vz of Ypq * vz^r
-  const R D000 = Y00[0] + Y00[1] + Y00[2], D001 = Y00[2] - Y00[0], D002 = Y00[2] + Y00[0];
-  const R D100 = Y10[0] + Y10[1] + Y10[2], D101 = Y10[2] - Y10[0], D102 = Y10[2] + Y10[0];
-  const R D010 = Y01[0] + Y01[1] + Y01[2], D011 = Y01[2] - Y01[0], D012 = Y01[2] + Y01[0];
-  const R D200 = Y20[0] + Y20[1] + Y20[2], D201 = Y20[2] - Y20[0];
-  const R D020 = Y02[0] + Y02[1] + Y02[2], D021 = Y02[2] - Y02[0];
-  const R D110 = Y11[0] + Y11[1] + Y11[2], D111 = Y11[2] - Y11[0];
-  const R D120 = Y12[0] + Y12[1] + Y12[2];
-  const R D210 = Y21[0] + Y21[1] + Y21[2];
+  auto zsum = [](const R (&Y)[3]) { return O::add(O::add(Y[0], Y[2]), Y[1]); };
+  const R D000 = zsum(Y00), D001 = O::sub(Y00[2], Y00[0]), D002 = O::add(Y00[2], Y00[0]);
+  const R D100 = zsum(Y10), D101 = O::sub(Y10[2], Y10[0]), D102 = O::add(Y10[2], Y10[0]);
+  const R D010 = zsum(Y01), D011 = O::sub(Y01[2], Y01[0]), D012 = O::add(Y01[2], Y01[0]);
+  const R D200 = zsum(Y20), D201 = O::sub(Y20[2], Y20[0]);
+  const R D020 = zsum(Y02), D021 = O::sub(Y02[2], Y02[0]);
+  const R D110 = zsum(Y11), D111 = O::sub(Y11[2], Y11[0]);
+  const R D120 = zsum(Y12);
+  const R D210 = zsum(Y21);
 
   // ---- conserved quantities (listing step 1); sum W = 1, sum W v = 0
+  const R one = R(1), three = R(3);
   const R drho = D000;
-  const R rho = R(1) + drho;
-  const R ir = R(1) / rho;
-  const R ux = D100 * ir, uy = D010 * ir, uz = D001 * ir;
+  const R rho = O::add(one, drho);
+  const R ir = O::div(one, rho);
+  const R ux = O::mul(D100, ir), uy = O::mul(D010, ir), uz = O::mul(D001, ir);
 
-  // ---- per-axis equilibrium factors (listing step 2)
-  const R Rx = rsq<R>(R(1) + R(3) * ux * ux);
-  const R Ry = rsq<R>(R(1) + R(3) * uy * uy);
-  const R Rz = rsq<R>(R(1) + R(3) * uz * uz);
-  const R ex = R(3) * ux * ux / (R(1) + Rx);   // R - 1 without cancellation
-  const R ey = R(3) * uy * uy / (R(1) + Ry);
-  const R ez = R(3) * uz * uz / (R(1) + Rz);
-  const R m2x = R(1.0 / 3.0) + R(2.0 / 3.0) * ex;  // m_2(u) = (2R - 1)/3
-  const R m2y = R(1.0 / 3.0) + R(2.0 / 3.0) * ey;
-  const R m2z = R(1.0 / 3.0) + R(2.0 / 3.0) * ez;
+  // ---- per-axis equilibrium factors (listing step 2): e = R - 1 = 3u^2 / (1 + R)
+  auto axis_e = [&](R u) {
+    const R u3 = O::mul(three, O::mul(u, u));
+    const R Rr = O::sqrt(O::add(one, u3));
+    return O::div(u3, O::add(one, Rr));
+  };
+  const R ex = axis_e(ux), ey = axis_e(uy), ez = axis_e(uz);
+  const R c23 = R(2.0 / 3.0), c13 = R(1.0 / 3.0);
+  const R m2x = O::fma(c23, ex, c13);  // m_2(u) = (2R - 1)/3
+  const R m2y = O::fma(c23, ey, c13);
+  const R m2z = O::fma(c23, ez, c13);
 
   // ---- rho-scaled moment deviations rho (M - M_eq) (listing steps 3-4)
-  const R d3 = drho * R(1.0 / 3.0);
-  const R A200 = (D200 - d3) - rho * (R(2.0 / 3.0) * ex);
-  const R A020 = (D020 - d3) - rho * (R(2.0 / 3.0) * ey);
-  const R A002 = (D002 - d3) - rho * (R(2.0 / 3.0) * ez);
-  const R ANxz = A200 - A002, ANyz = A020 - A002;
-  const R AT = cp.with_t ? (A200 + A020 + A002) : R(0);
-  const R APxy = D110 - D100 * uy, APxz = D101 - D100 * uz, APyz = D011 - D010 * uz;
+  const R rc23 = O::mul(rho, c23);
+  const R nd3 = O::mul(drho, -c13);
+  const R A200 = O::fma(-rc23, ex, O::add(D200, nd3));
+  const R A020 = O::fma(-rc23, ey, O::add(D020, nd3));
+  const R A002 = O::fma(-rc23, ez, O::add(D002, nd3));
+  const R ANxz = O::sub(A200, A002), ANyz = O::sub(A020, A002);
+  const R AT = cp.with_t ? O::add(O::add(A200, A020), A002) : R(0);
+  const R APxy = O::fma(-D100, uy, D110), APxz = O::fma(-D100, uz, D101);
+  const R APyz = O::fma(-D010, uz, D011);
   const R qs = cp.with_q ? R(1) : R(0);
-  const R AQxyy = qs * (D120 - D100 * m2y), AQxzz = qs * (D102 - D100 * m2z);
-  const R AQxxy = qs * (D210 - D010 * m2x), AQyzz = qs * (D012 - D010 * m2z);
-  const R AQxxz = qs * (D201 - D001 * m2x), AQyyz = qs * (D021 - D001 * m2y);
-  const R AQxyz = qs * (D111 - D100 * uy * uz);
+  const R AQxyy = O::mul(qs, O::fma(-D100, m2y, D120)), AQxzz = O::mul(qs, O::fma(-D100, m2z, D102));
+  const R AQxxy = O::mul(qs, O::fma(-D010, m2x, D210)), AQyzz = O::mul(qs, O::fma(-D010, m2z, D012));
+  const R AQxxz = O::mul(qs, O::fma(-D001, m2x, D201)), AQyyz = O::mul(qs, O::fma(-D001, m2y, D021));
+  const R AQxyz = O::mul(qs, O::fma(-O::mul(D100, uy), uz, D111));
 
   // Table 1 per velocity class: ds = d + t + q evaluated on the deviations
+  const R c16 = R(1.0 / 6.0), half = R(0.5), quarter = R(0.25);
   const R s0 = -AT;
-  const R Fx = (R(2) * ANxz - ANyz + AT) * R(1.0 / 6.0), Gx = (AQxyy + AQxzz) * R(0.5);
-  const R Fy = (R(2) * ANyz - ANxz + AT) * R(1.0 / 6.0), Gy = (AQxxy + AQyzz) * R(0.5);
-  const R Fz = (AT - ANxz - ANyz) * R(1.0 / 6.0), Gz = (AQxxz + AQyyz) * R(0.5);
-  const R Pxy4 = R(0.25) * APxy, Pxz4 = R(0.25) * APxz, Pyz4 = R(0.25) * APyz;
-  const R Qxxy4 = R(0.25) * AQxxy, Qxyy4 = R(0.25) * AQxyy, Qxxz4 = R(0.25) * AQxxz;
-  const R Qxzz4 = R(0.25) * AQxzz, Qyyz4 = R(0.25) * AQyyz, Qyzz4 = R(0.25) * AQyzz;
-  const R Qxyz8 = R(0.125) * AQxyz;
+  const R Fx = O::mul(O::add(O::sub(O::add(ANxz, ANxz), ANyz), AT), c16);
+  const R Fy = O::mul(O::add(O::sub(O::add(ANyz, ANyz), ANxz), AT), c16);
+  const R Fz = O::mul(O::sub(O::sub(AT, ANxz), ANyz), c16);
+  const R Gx = O::mul(O::add(AQxyy, AQxzz), half);
+  const R Gy = O::mul(O::add(AQxxy, AQyzz), half);
+  const R Gz = O::mul(O::add(AQxxz, AQyyz), half);
+  const R Pxy4 = O::mul(quarter, APxy), Pxz4 = O::mul(quarter, APxz);
+  const R Pyz4 = O::mul(quarter, APyz);
+  const R Qxxy4 = O::mul(quarter, AQxxy), Qxyy4 = O::mul(quarter, AQxyy);
+  const R Qxxz4 = O::mul(quarter, AQxxz), Qxzz4 = O::mul(quarter, AQxzz);
+  const R Qyyz4 = O::mul(quarter, AQyyz), Qyzz4 = O::mul(quarter, AQyzz);
+  const R Qxyz8 = O::mul(R(0.125), AQxyz);
+  auto sg = [](int s, R v) { return s > 0 ? v : -v; };
+  // (s1 P) + (s2 Q1) + (s3 Q2) for an edge class; signs are compile-time after unrolling
+  auto edge = [&](int sp, R P4, int s1, R Q1, int s2, R Q2) {
+    return O::add(O::add(sg(sp, P4), sg(s1, Q1)), sg(s2, Q2));
+  };
   auto ds_of = [&](int a, int b, int c) -> R {
     const int nnz = (a != 0) + (b != 0) + (c != 0);
     if (nnz == 0) return s0;
     if (nnz == 1) {
-      if (a != 0) return a > 0 ? Fx - Gx : Fx + Gx;
-      if (b != 0) return b > 0 ? Fy - Gy : Fy + Gy;
-      return c > 0 ? Fz - Gz : Fz + Gz;
+      if (a != 0) return a > 0 ? O::sub(Fx, Gx) : O::add(Fx, Gx);
+      if (b != 0) return b > 0 ? O::sub(Fy, Gy) : O::add(Fy, Gy);
+      return c > 0 ? O::sub(Fz, Gz) : O::add(Fz, Gz);
     }
     if (nnz == 2) {
-      if (c == 0) return R(a * b) * Pxy4 + R(b) * Qxxy4 + R(a) * Qxyy4;
-      if (b == 0) return R(a * c) * Pxz4 + R(c) * Qxxz4 + R(a) * Qxzz4;
-      return R(b * c) * Pyz4 + R(c) * Qyyz4 + R(b) * Qyzz4;
+      if (c == 0) return edge(a * b, Pxy4, b, Qxxy4, a, Qxyy4);
+      if (b == 0) return edge(a * c, Pxz4, c, Qxxz4, a, Qxzz4);
+      return edge(b * c, Pyz4, c, Qyyz4, b, Qyzz4);
     }
-    return R(a * b * c) * Qxyz8;
+    return sg(a * b * c, Qxyz8);
   };
 
-  // equilibrium factors: rho phi_x(a) = W_a (1 + gx_a), phi_y(b) = W_b (1 + ey_b), ...
-  const R gx[3] = {drho + (R(2) * ex - R(3) * ux) * rho, drho - ex * rho,
-                   drho + (R(2) * ex + R(3) * ux) * rho};
-  const R fy[3] = {R(2) * ey - R(3) * uy, -ey, R(2) * ey + R(3) * uy};
-  const R fz[3] = {R(2) * ez - R(3) * uz, -ez, R(2) * ez + R(3) * uz};
+  // equilibrium factors: rho phi_x(a) = W_a (1 + gx_a), phi_y(b) = W_b (1 + fy_b), ...
+  // with e_0 = -e, e_{+-1} = 2e +- 3u; the x factor carries rho: gx = drho + rho e_x
+  const R two = R(2);
+  const R tex = O::add(ex, ex), tey = O::add(ey, ey), tez = O::add(ez, ez);
+  const R ux3 = O::mul(three, ux), uy3 = O::mul(three, uy), uz3 = O::mul(three, uz);
+  const R gx[3] = {O::fma(rho, O::sub(tex, ux3), drho), O::fma(-rho, ex, drho),
+                   O::fma(rho, O::add(tex, ux3), drho)};
+  const R fy[3] = {O::sub(tey, uy3), -ey, O::add(tey, uy3)};
+  const R fz[3] = {O::sub(tez, uz3), -ez, O::add(tez, uz3)};
+  (void)two;
   // reciprocal weights of the entropic scalar product, 1/f_eq_i = rx[a] ry[b] rz[c]
+  auto recip_axis = [&](const R (&e)[3], R (&r)[3]) {
+    const R p0 = O::mul(c16, O::add(one, e[0]));
+    const R p1 = O::mul(c23, O::add(one, e[1]));
+    const R p2 = O::mul(c16, O::add(one, e[2]));
+    const R p12 = O::mul(p1, p2);
+    const R q = O::div(one, O::mul(p0, p12));   // one division for three reciprocals
+    const R qp0 = O::mul(q, p0);
+    r[0] = O::mul(p12, q);
+    r[1] = O::mul(p2, qp0);
+    r[2] = O::mul(p1, qp0);
+  };
   R rx[3], ry[3], rz[3];
-  recip3<R>(R(1.0 / 6.0) * (R(1) + gx[0]), R(2.0 / 3.0) * (R(1) + gx[1]),
-            R(1.0 / 6.0) * (R(1) + gx[2]), rx[0], rx[1], rx[2]);
-  recip3<R>(R(1.0 / 6.0) * (R(1) + fy[0]), R(2.0 / 3.0) * (R(1) + fy[1]),
-            R(1.0 / 6.0) * (R(1) + fy[2]), ry[0], ry[1], ry[2]);
-  recip3<R>(R(1.0 / 6.0) * (R(1) + fz[0]), R(2.0 / 3.0) * (R(1) + fz[1]),
-            R(1.0 / 6.0) * (R(1) + fz[2]), rz[0], rz[1], rz[2]);
+  recip_axis(gx, rx);
+  recip_axis(fy, ry);
+  recip_axis(fz, rz);
 
   // ---- dh, the two entropic products, and the part of the relaxation known before gamma
   // (listing steps 5-6): d <- d - 2 beta ds, dh kept for the gamma-dependent part
-  const R b2 = R(cp.two_beta);
+  const R nb2 = R(-cp.two_beta);
   R dh[27];
   R num = R(0), den = R(0);
 #pragma unroll
@@ -229,28 +268,26 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, bool* 
     R cn = R(0), cd = R(0);
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      const R Pab0 = gx[0] + fy[b] + gx[0] * fy[b];
-      const R Pab1 = gx[1] + fy[b] + gx[1] * fy[b];
-      const R Pab2 = gx[2] + fy[b] + gx[2] * fy[b];
-      const R Pab[3] = {Pab0, Pab1, Pab2};
       R rn = R(0), rd = R(0);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const int i = a + 3 * b + 9 * c;
-        const R G = Pab[a] + fz[c] + Pab[a] * fz[c];      // (f_eq_i - W_i) / W_i
+        // (f_eq_i - W_i)/W_i = (1 + gx)(1 + fy)(1 + fz) - 1 without cancellation
+        const R P = O::fma(gx[a], fy[b], O::add(gx[a], fy[b]));
+        const R G = O::fma(P, fz[c], O::add(P, fz[c]));
         const R dsi = ds_of(a - 1, b - 1, c - 1);
-        const R dhi = d[i] - R(wgt(i)) * G - dsi;
-        const R t1 = rx[a] * dhi;
-        rn += t1 * dsi;
-        rd += t1 * dhi;
+        const R dhi = O::sub(O::fma(R(-wgt(i)), G, d[i]), dsi);
+        const R t1 = O::mul(rx[a], dhi);
+        rn = O::fma(t1, dsi, rn);
+        rd = O::fma(t1, dhi, rd);
         dh[i] = dhi;
-        d[i] -= b2 * dsi;
+        d[i] = O::fma(nb2, dsi, d[i]);
       }
-      cn += ry[b] * rn;
-      cd += ry[b] * rd;
+      cn = O::fma(ry[b], rn, cn);
+      cd = O::fma(ry[b], rd, cd);
     }
-    num += rz[c] * cn;
-    den += rz[c] * cd;
+    num = O::fma(rz[c], cn, num);
+    den = O::fma(rz[c], cd, den);
   }
 
   // ---- stabilizer (eq:result21) and the rest of the relaxation (listing step 7)
@@ -262,16 +299,16 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, bool* 
   } else if (cp.gamma_mode == GAMMA_RLB) {
     gamma = ib;
   } else if (den > Guard<R>::den) {
-    gamma = ib - (R(2) - ib) * (num / den);
+    gamma = O::fma(-O::sub(R(2), ib), O::div(num, den), ib);
   } else if (den == den) {
     gamma = R(2);
     *guarded = true;
   } else {
     gamma = den;  // NaN propagates to the populations and to the diagnostics
   }
-  const R bg = R(cp.beta) * gamma;
+  const R nbg = -O::mul(R(cp.beta), gamma);
 #pragma unroll
-  for (int i = 0; i < 27; ++i) d[i] -= bg * dh[i];
+  for (int i = 0; i < 27; ++i) d[i] = O::fma(nbg, dh[i], d[i]);
   return gamma;
 }
 

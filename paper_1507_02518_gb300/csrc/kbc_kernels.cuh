@@ -228,6 +228,29 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[N], double* dst) 
   }
 }
 
+// rho and rho u of canonical f(t) at one node in the arithmetic type of the storage
+template <typename S>
+__device__ __forceinline__ void node_moments_r(const S* b0, const S* b1, const Geo& g,
+                                               const Nbr& nb, int scheme, int parity,
+                                               typename Codec<S>::R& rho,
+                                               typename Codec<S>::R (&m)[3]) {
+  using R = typename Codec<S>::R;
+  R s = R(0), mx = R(0), my = R(0), mz = R(0);
+#pragma unroll
+  for (int i = 0; i < 27; ++i) {
+    const R dv = (R)Codec<S>::to_delta(*canon_addr<S>((S*)b0, (S*)b1, g, nb, scheme, parity, i), i);
+    s += dv;
+    if (cx(i)) mx += cx(i) * dv;
+    if (cy(i)) my += cy(i) * dv;
+    if (cz(i)) mz += cz(i) * dv;
+  }
+  rho = R(1) + s;
+  m[0] = mx;
+  m[1] = my;
+  m[2] = mz;
+}
+
+// Per-node quantities in the storage's arithmetic type; per-thread and global sums in FP64.
 template <typename S>
 __global__ void __launch_bounds__(256) diag_fields_kernel(const S* b0, const S* b1, Geo g,
                                                           int scheme, int parity,
@@ -242,24 +265,25 @@ __global__ void __launch_bounds__(256) diag_fields_kernel(const S* b0, const S* 
     node_coords(g, n, x, y, z);
     Nbr nb;
     nb.init(g, x, y, z);
-    double rho, m[3];
-    node_moments<S>(b0, b1, g, nb, scheme, parity, rho, m);
-    const double ux = m[0] / rho, uy = m[1] / rho, uz = m[2] / rho;
-    uf[n] = (R)ux;
-    uf[g.P + n] = (R)uy;
-    uf[2 * g.P + n] = (R)uz;
+    R rho, m[3];
+    node_moments_r<S>(b0, b1, g, nb, scheme, parity, rho, m);
+    const R ir = R(1) / rho;
+    const R ux = m[0] * ir, uy = m[1] * ir, uz = m[2] * ir;
+    uf[n] = ux;
+    uf[g.P + n] = uy;
+    uf[2 * g.P + n] = uz;
     if (!isfinite(rho) || !isfinite(ux) || !isfinite(uy) || !isfinite(uz)) {
       v[10] += 1.0;
       continue;
     }
-    v[0] += rho;
-    v[1] += m[0];
-    v[2] += m[1];
-    v[3] += m[2];
-    v[4] += ux;
-    v[5] += uy;
-    v[6] += uz;
-    v[7] += ux * ux + uy * uy + uz * uz;
+    v[0] += (double)rho;
+    v[1] += (double)m[0];
+    v[2] += (double)m[1];
+    v[3] += (double)m[2];
+    v[4] += (double)ux;
+    v[5] += (double)uy;
+    v[6] += (double)uz;
+    v[7] += (double)(ux * ux + uy * uy + uz * uz);
     if (with_gamma) {
       const double gm = gamma[n];
       v[8] += gm;
@@ -278,32 +302,29 @@ __global__ void __launch_bounds__(256) diag_grad_kernel(Geo g, const R* uf, doub
     node_coords(g, n, x, y, z);
     Nbr nb;
     nb.init(g, x, y, z);
-    const uint32_t here = nb.ox[1] + nb.oy[1] + nb.oz[1];
     // neighbours along +-x, +-y, +-z
     const uint32_t np[3] = {nb.ox[2] + nb.oy[1] + nb.oz[1], nb.ox[1] + nb.oy[2] + nb.oz[1],
                             nb.ox[1] + nb.oy[1] + nb.oz[2]};
     const uint32_t nm[3] = {nb.ox[0] + nb.oy[1] + nb.oz[1], nb.ox[1] + nb.oy[0] + nb.oz[1],
                             nb.ox[1] + nb.oy[1] + nb.oz[0]};
-    (void)here;
-    double gr[3][3];  // gr[a][b] = d u_a / d x_b, second-order central difference
+    R gr[3][3];  // gr[a][b] = d u_a / d x_b, second-order central difference
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-      for (int b = 0; b < 3; ++b)
-        gr[a][b] = 0.5 * ((double)uf[a * g.P + np[b]] - (double)uf[a * g.P + nm[b]]);
-    const double wx = gr[2][1] - gr[1][2], wy = gr[0][2] - gr[2][0], wz = gr[1][0] - gr[0][1];
-    const double ww = wx * wx + wy * wy + wz * wz;
-    double ss = 0.0;
+      for (int b = 0; b < 3; ++b) gr[a][b] = R(0.5) * (uf[a * g.P + np[b]] - uf[a * g.P + nm[b]]);
+    const R wx = gr[2][1] - gr[1][2], wy = gr[0][2] - gr[2][0], wz = gr[1][0] - gr[0][1];
+    const R ww = wx * wx + wy * wy + wz * wz;
+    R ss = R(0);
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
-        const double s = gr[a][b] + gr[b][a];
+        const R s = gr[a][b] + gr[b][a];
         ss += s * s;
       }
     if (isfinite(ww) && isfinite(ss)) {
-      v[0] += ww;
-      v[1] += ss;
+      v[0] += (double)ww;
+      v[1] += (double)ss;
     }
   }
   block_reduce_store<2>(v, partials + blockIdx.x * kDiagSums + 11);

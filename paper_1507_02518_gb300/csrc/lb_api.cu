@@ -733,10 +733,12 @@ lb_status lb_batch_step(lb_batch* b, int64_t n) {
   if (!b) return LB_ERR_INVALID_ARG;
   if (n < 0) return bfail(b, LB_ERR_INVALID_ARG, "n must be >= 0");
   if (n == 0) return LB_OK;
+  // all boxes must share one time (initialising a box resets its t to 0)
   for (lb_ctx* v : b->views)
-    if (v->t != b->t)
-      return bfail(b, LB_ERR_INVALID_ARG, "a box was stepped or re-timed on its own; all boxes "
-                                          "of a batch must share the time t");
+    if (v->t != b->views[0]->t)
+      return bfail(b, LB_ERR_INVALID_ARG, "boxes of a batch are at different times; step, "
+                                          "initialise or re-time all of them together");
+  b->t = b->views[0]->t;
   const auto key = std::make_pair(n, (int)(b->t & 1));
   auto it = b->graphs.find(key);
   if (it == b->graphs.end()) {
@@ -817,6 +819,7 @@ lb_status lb_batch_autotune(lb_batch* b, int32_t trial_steps, int32_t* best_thre
     return bfail(b, LB_ERR_CUDA, "creating timing events");
   double best = 1e300;
   int bt = b->threads, bl = b->tile;
+  b->t = b->views[0]->t;
   lb_status st = LB_OK;
   for (int th : cand_threads) {
     if (th > maxt) continue;
