@@ -137,10 +137,25 @@ double lb_beta(const lb_ctx *ctx);
  * lb_set_populations). t >= 0. */
 lb_status lb_set_time(lb_ctx *ctx, int64_t t);
 
-/* Launch shape of the step kernel: threads per block along x (bx) and y (by), with
- * bx*by in {64, 128, 256, 512} and bx a multiple of 32. Defaults to (128, 1) or the
- * shape the autotuner chose. */
+/* Which step kernel runs. LB_KERNEL_STAGED stages the 27 source rows of each 128-node
+ * x-segment in shared memory with asynchronous bulk copies (a pipelined persistent grid); it
+ * needs nx * sizeof(stored value) to be a multiple of 16 bytes (else LB_ERR_UNSUPPORTED).
+ * LB_KERNEL_DIRECT loads straight from global memory, one thread per node, any nx.
+ * LB_KERNEL_AUTO (default) takes the staged kernel whenever it applies. All kernels produce
+ * bit-identical populations. */
+enum { LB_KERNEL_AUTO = 0, LB_KERNEL_DIRECT = 1, LB_KERNEL_STAGED = 2 };
+lb_status lb_set_kernel(lb_ctx *ctx, int32_t kind);
+
+/* Launch shape of the direct kernel: threads per block along x (bx) and y (by), with
+ * bx*by in {64, 128, 256, 512} (at most 256 for LB_F64) and bx a multiple of 32. */
 lb_status lb_set_block(lb_ctx *ctx, int32_t bx, int32_t by);
+
+/* Bound on every device-side wait of the staged kernel, in SM clock cycles (default 2e9,
+ * about one second). When a wait runs out the kernel sets a flag and returns; the next
+ * synchronising call returns LB_ERR_TIMEOUT and the state is not valid. stall_copies != 0
+ * is a test hook of that path: the staged kernel then issues no copies, so its first wait
+ * runs out (use a small budget). */
+lb_status lb_set_wait_budget(lb_ctx *ctx, uint64_t cycles, int32_t stall_copies);
 
 /* ---------------------------------------------------------------- batched ensemble
  * Many independent periodic boxes of uneven sizes and viscosities, stepped together: one

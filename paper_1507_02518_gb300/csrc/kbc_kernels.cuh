@@ -9,6 +9,7 @@
 
 #include "kbc_device.cuh"
 #include "kbc_ops.h"
+#include "kbc_staged.cuh"
 
 namespace kbc {
 
@@ -369,36 +370,43 @@ inline int grid_for(uint64_t cnt, int threads) {
   return (int)blocks;
 }
 
+template <typename S, int MODE, bool RECORD>
+static cudaError_t launch_step(const BoxView& b, const S* src, S* dst, const Geo& g,
+                               const CollideParams& cp, const StepOpts& o, StepCounters* ctr,
+                               cudaStream_t st) {
+  const bool staged = o.kernel == KERNEL_STAGED ||
+                      (o.kernel == KERNEL_AUTO && staged_supported<S>(b.nx));
+  if (staged)
+    return launch_staged<S, MODE, RECORD>(src, dst, g, cp, b.gamma, ctr, o.budget, o.stall, st);
+  const dim3 block(o.bx, o.by, 1);
+  const dim3 grid((b.nx + o.bx - 1) / o.bx, (b.ny + o.by - 1) / o.by, b.nz);
+  step_kernel<S, MODE, RECORD><<<grid, block, 0, st>>>(src, dst, g, cp, b.gamma, ctr);
+  return cudaGetLastError();
+}
+
 template <typename S>
-cudaError_t Ops<S>::step(const BoxView& b, int64_t t, bool record, int bx, int by,
+bool Ops<S>::staged_ok(uint32_t nx) {
+  return staged_supported<S>(nx);
+}
+
+template <typename S>
+cudaError_t Ops<S>::step(const BoxView& b, int64_t t, bool record, const StepOpts& o,
                          StepCounters* counters, cudaStream_t st) {
   const Geo g = make_geo(b);
   const CollideParams cp = make_cp(b.beta, b.with_t, b.with_q, b.gamma_mode);
-  const dim3 block(bx, by, 1);
-  const dim3 grid((b.nx + bx - 1) / bx, (b.ny + by - 1) / by, b.nz);
   const int parity = (int)(t & 1);
   if (b.scheme == 0) {
     const S* src = (const S*)b.pop[parity];
     S* dst = (S*)b.pop[parity ^ 1];
-    if (record)
-      step_kernel<S, MODE_PULL, true><<<grid, block, 0, st>>>(src, dst, g, cp, b.gamma, counters);
-    else
-      step_kernel<S, MODE_PULL, false><<<grid, block, 0, st>>>(src, dst, g, cp, b.gamma, counters);
-  } else {
-    S* buf = (S*)b.pop[0];
-    if (parity == 0) {
-      if (record)
-        step_kernel<S, MODE_AA_EVEN, true><<<grid, block, 0, st>>>(buf, buf, g, cp, b.gamma, counters);
-      else
-        step_kernel<S, MODE_AA_EVEN, false><<<grid, block, 0, st>>>(buf, buf, g, cp, b.gamma, counters);
-    } else {
-      if (record)
-        step_kernel<S, MODE_AA_ODD, true><<<grid, block, 0, st>>>(buf, buf, g, cp, b.gamma, counters);
-      else
-        step_kernel<S, MODE_AA_ODD, false><<<grid, block, 0, st>>>(buf, buf, g, cp, b.gamma, counters);
-    }
+    return record ? launch_step<S, MODE_PULL, true>(b, src, dst, g, cp, o, counters, st)
+                  : launch_step<S, MODE_PULL, false>(b, src, dst, g, cp, o, counters, st);
   }
-  return cudaGetLastError();
+  S* buf = (S*)b.pop[0];
+  if (parity == 0)
+    return record ? launch_step<S, MODE_AA_EVEN, true>(b, buf, buf, g, cp, o, counters, st)
+                  : launch_step<S, MODE_AA_EVEN, false>(b, buf, buf, g, cp, o, counters, st);
+  return record ? launch_step<S, MODE_AA_ODD, true>(b, buf, buf, g, cp, o, counters, st)
+                : launch_step<S, MODE_AA_ODD, false>(b, buf, buf, g, cp, o, counters, st);
 }
 
 template <typename S>

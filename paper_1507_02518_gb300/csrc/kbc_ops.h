@@ -16,9 +16,21 @@ struct BoxView {
   int scheme;          // 0 pull, 1 AA
 };
 
-// counters written by the step kernel when it records gamma
+// counters written by the step kernels: guard events of the recorded collision, and a flag
+// set when a bounded device-side wait ran out
 struct StepCounters {
   unsigned long long guarded;
+  unsigned int timeout;
+  unsigned int pad;
+};
+
+// kernel choice and test hooks of one step launch
+enum { KERNEL_AUTO = 0, KERNEL_DIRECT = 1, KERNEL_STAGED = 2 };
+struct StepOpts {
+  int bx, by;                 // block of the direct kernel
+  int kernel;                 // KERNEL_*
+  unsigned long long budget;  // wait budget (SM cycles) of the staged kernel
+  int stall;                  // test hook: the staged kernel issues no copies
 };
 
 // one item of the batched work list: rows [row0, row0 + nrows) of box `box`
@@ -41,8 +53,10 @@ struct BoxDesc {
 
 template <typename S> struct Ops {
   // one time step t -> t+1 of one box; `record` writes gamma and counts guards
-  static cudaError_t step(const BoxView& b, int64_t t, bool record, int bx, int by,
+  static cudaError_t step(const BoxView& b, int64_t t, bool record, const StepOpts& o,
                           StepCounters* counters, cudaStream_t st);
+  // whether the staged (bulk-copy pipelined) kernel supports this row length
+  static bool staged_ok(uint32_t nx);
   // canonical f(t) = f_eq(rho, u) for nodes [n0, n0 + cnt) (rho may be null: 1)
   static cudaError_t init(const BoxView& b, int64_t t, const double* rho, const double* u,
                           uint64_t n0, uint64_t cnt, uint64_t ld, cudaStream_t st);

@@ -142,6 +142,9 @@ struct lb_ctx {
   double* staging = nullptr;
   uint64_t stage_nodes = 0;
   int bx = 128, by = 1;
+  int kernel = kbc::KERNEL_AUTO;
+  unsigned long long wait_budget = 2000000000ull;  // about 1 s at the SM clock
+  int stall = 0;
   bool gamma_valid = false;
   bool batch_view = false;
   std::string err;
@@ -211,10 +214,32 @@ lb_status zero_state(lb_ctx* c) {
   return LB_OK;
 }
 
+// Synchronise the stream, then surface a bounded-wait timeout flagged by a step kernel.
 lb_status sync(lb_ctx* c, const char* what) {
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, what);
+  unsigned int flag = 0;
+  e = cudaMemcpyAsync(&flag, &c->counters->timeout, sizeof flag, cudaMemcpyDeviceToHost,
+                      c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, what);
+  if (flag) {
+    cudaMemsetAsync(&c->counters->timeout, 0, sizeof flag, c->stream);
+    cudaStreamSynchronize(c->stream);
+    return fail(c, LB_ERR_TIMEOUT, std::string(what) + ": a step kernel's bounded wait for its "
+                                   "staged loads ran out; the state is not valid");
+  }
   return LB_OK;
+}
+
+kbc::StepOpts step_opts(const lb_ctx* c) {
+  kbc::StepOpts o;
+  o.bx = c->bx;
+  o.by = c->by;
+  o.kernel = c->kernel;
+  o.budget = c->wait_budget;
+  o.stall = c->stall;
+  return o;
 }
 
 }  // namespace
@@ -319,10 +344,10 @@ lb_status lb_step(lb_ctx* c, int64_t n) {
   for (int64_t k = 0; k < n; ++k) {
     const bool record = (k == n - 1);
     cudaError_t e = cudaSuccess;
-    if (record) e = cudaMemsetAsync(c->counters, 0, sizeof(kbc::StepCounters), c->stream);
+    if (record) e = cudaMemsetAsync(&c->counters->guarded, 0, sizeof(unsigned long long), c->stream);
     if (e == cudaSuccess)
       e = dispatch(c, [&](auto ops) {
-        return ops.step(c->box, c->t, record, c->bx, c->by, c->counters, c->stream);
+        return ops.step(c->box, c->t, record, step_opts(c), c->counters, c->stream);
       });
     if (e != cudaSuccess) return cuda_fail(c, e, "step kernel");
     c->t += 1;
@@ -456,6 +481,32 @@ lb_status lb_set_time(lb_ctx* c, int64_t t) {
   if (t < 0) return fail(c, LB_ERR_INVALID_ARG, "t must be >= 0");
   c->t = t;
   c->gamma_valid = false;
+  return LB_OK;
+}
+
+lb_status lb_set_kernel(lb_ctx* c, int32_t kind) {
+  if (!c) return LB_ERR_INVALID_ARG;
+  if (kind != LB_KERNEL_AUTO && kind != LB_KERNEL_DIRECT && kind != LB_KERNEL_STAGED)
+    return fail(c, LB_ERR_INVALID_ARG, "kind must be LB_KERNEL_AUTO, _DIRECT or _STAGED");
+  if (kind == LB_KERNEL_STAGED) {
+    bool ok = false;
+    dispatch(c, [&](auto ops) {
+      ok = ops.staged_ok(c->box.nx);
+      return cudaSuccess;
+    });
+    if (!ok)
+      return fail(c, LB_ERR_UNSUPPORTED, "the staged kernel needs nx * sizeof(value) to be a "
+                                         "multiple of 16 bytes");
+  }
+  c->kernel = kind;
+  return LB_OK;
+}
+
+lb_status lb_set_wait_budget(lb_ctx* c, uint64_t cycles, int32_t stall_copies) {
+  if (!c) return LB_ERR_INVALID_ARG;
+  if (cycles == 0) return fail(c, LB_ERR_INVALID_ARG, "cycles must be > 0");
+  c->wait_budget = cycles;
+  c->stall = stall_copies ? 1 : 0;
   return LB_OK;
 }
 
@@ -752,7 +803,8 @@ lb_status lb_batch_step(lb_batch* b, int64_t n) {
       if (record) {
         for (lb_ctx* v : b->views)
           if (le == cudaSuccess)
-            le = cudaMemsetAsync(v->counters, 0, sizeof(kbc::StepCounters), b->capture_stream);
+            le = cudaMemsetAsync(&v->counters->guarded, 0, sizeof(unsigned long long),
+                                 b->capture_stream);
       }
       if (le == cudaSuccess) le = enqueue_batch_step(b, b->t + k, record, b->capture_stream);
     }

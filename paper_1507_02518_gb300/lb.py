@@ -22,6 +22,8 @@ LB_S_D, LB_S_DT, LB_S_DQ, LB_S_DTQ = range(4)
 LB_GAMMA_ESTIMATE, LB_GAMMA_LBGK, LB_GAMMA_RLB = range(3)
 LB_F64, LB_F32, LB_F16 = range(3)
 LB_PULL, LB_AA = range(2)
+LB_KERNEL_AUTO, LB_KERNEL_DIRECT, LB_KERNEL_STAGED = range(3)
+KERNEL = {"auto": LB_KERNEL_AUTO, "direct": LB_KERNEL_DIRECT, "staged": LB_KERNEL_STAGED}
 
 STORAGE = {"f64": LB_F64, "f32": LB_F32, "f16": LB_F16}
 SCHEME = {"pull": LB_PULL, "aa": LB_AA}
@@ -60,6 +62,7 @@ _lock = threading.Lock()
 SYMBOLS = ["lb_required_bytes", "lb_create", "lb_destroy", "lb_last_error", "lb_init_field",
            "lb_step", "lb_moments", "lb_diagnostics", "lb_get_populations",
            "lb_set_populations", "lb_time", "lb_beta", "lb_set_time", "lb_set_block",
+           "lb_set_kernel", "lb_set_wait_budget",
            "lb_batch_required_bytes", "lb_batch_create", "lb_batch_destroy",
            "lb_batch_last_error", "lb_batch_box", "lb_batch_step", "lb_batch_diagnostics",
            "lb_batch_autotune", "lb_batch_set_tile"]
@@ -111,6 +114,10 @@ def load(path: str = LIB_PATH):
         L.lb_set_time.argtypes = [vp, i64]
         L.lb_set_block.restype = i32
         L.lb_set_block.argtypes = [vp, i32, i32]
+        L.lb_set_kernel.restype = i32
+        L.lb_set_kernel.argtypes = [vp, i32]
+        L.lb_set_wait_budget.restype = i32
+        L.lb_set_wait_budget.argtypes = [vp, ctypes.c_uint64, i32]
         L.lb_batch_required_bytes.restype = ctypes.c_size_t
         L.lb_batch_required_bytes.argtypes = [cfgp, i32]
         L.lb_batch_create.restype = i32
@@ -218,6 +225,14 @@ def lb_set_time(ctx, t: int):
 
 def lb_set_block(ctx, bx: int, by: int):
     _check(load().lb_set_block(ctx, int(bx), int(by)), ctx)
+
+
+def lb_set_kernel(ctx, kind):
+    _check(load().lb_set_kernel(ctx, KERNEL[kind] if isinstance(kind, str) else int(kind)), ctx)
+
+
+def lb_set_wait_budget(ctx, cycles: int, stall_copies: bool = False):
+    _check(load().lb_set_wait_budget(ctx, int(cycles), int(bool(stall_copies))), ctx)
 
 
 def lb_batch_required_bytes(cfgs) -> int:
@@ -350,6 +365,9 @@ class Lattice:
 
     def set_block(self, bx, by):
         lb_set_block(self.ctx, bx, by)
+
+    def set_kernel(self, kind):
+        lb_set_kernel(self.ctx, kind)
 
     def save_checkpoint(self, path):
         """Raw little-endian FP64 canonical populations with a one-line JSON header."""

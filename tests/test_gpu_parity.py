@@ -162,6 +162,56 @@ def test_pull_and_aa_are_bitwise_identical(kbc, storage, steps):
     assert np.array_equal(out[0], out[1])
 
 
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("scheme", ["pull", "aa"])
+@pytest.mark.parametrize("shape", [(200, 3, 4), (256, 5, 3), (8, 6, 5)])
+def test_staged_and_direct_kernels_are_bitwise_identical(kbc, storage, scheme, shape):
+    """The shared-memory staged kernel (bulk copies, several x-segments, ragged last segment,
+    periodic wrap inside the staged rows) against the direct kernel."""
+    f0 = seeded_state(*shape, seed=9)
+    out = []
+    for kind in ("direct", "staged"):
+        lat = lattice(shape, storage=storage, scheme=scheme)
+        lat.set_kernel(kind)
+        lat.set_populations(f0)
+        lat.step(5)
+        out.append(lat.get_populations())
+    assert np.array_equal(out[0], out[1])
+    ref, _, _ = oracle.run(f0, 5, oracle.beta(1e-3))
+    tol = {"f64": FP64_TOL, "f32": 1e-6, "f16": 2e-3}[storage]
+    assert np.max(np.abs(out[1] - ref)) <= tol
+
+
+def test_staged_kernel_rejects_unaligned_rows(kbc):
+    lat = lattice((6, 4, 4), storage="f32")   # 24-byte rows
+    with pytest.raises(lb.LBError) as e:
+        lat.set_kernel("staged")
+    assert e.value.status == lb.LB_ERR_UNSUPPORTED
+
+
+def test_bounded_wait_reports_timeout_and_context_recovers(kbc):
+    """Test hook: the staged kernel issues no copies, so its first bounded wait runs out. The
+    kernel returns, the next synchronising call reports LB_ERR_TIMEOUT, and the context keeps
+    working once the hook is off."""
+    shape = (64, 8, 8)
+    f0 = seeded_state(*shape)
+    lat = lattice(shape, storage="f32", scheme="pull")
+    lat.set_kernel("staged")
+    lat.set_populations(f0)
+    lb.lb_set_wait_budget(lat.ctx, 200000, True)     # ~0.1 ms at 2 GHz
+    lat.step(1)
+    with pytest.raises(lb.LBError) as e:
+        lat.diagnostics()
+    assert e.value.status == lb.LB_ERR_TIMEOUT
+    lb.lb_set_wait_budget(lat.ctx, 2000000000, False)
+    lb.lb_set_time(lat.ctx, 0)
+    lat.set_populations(f0)
+    lat.step(3)
+    ref, _, _ = oracle.run(f0, 3, lat.beta)
+    assert np.max(np.abs(lat.get_populations() - ref)) <= 1e-6
+    lat.diagnostics()
+
+
 @pytest.mark.parametrize("scheme", ["pull", "aa"])
 def test_checkpoint_resume_is_bitwise(kbc, scheme, tmp_path):
     f0 = seeded_state(16, 8, 6)
