@@ -247,10 +247,12 @@ def run_box(w, steps, warmup, want_kernel_time=True):
     return out
 
 
-def run_batch(w, steps, warmup):
+def run_batch(w, steps, warmup, rank=0, world=1):
     import torch
-    from paper_1507_02518_gb300 import lb, workloads
+    from paper_1507_02518_gb300 import lb, sharding, workloads
     boxes = workloads.batch_boxes(w["nbox"])
+    if world > 1:                                 # LPT shard of the ensemble, no exchange
+        boxes, _ = sharding.shard_boxes(boxes, rank, world)
     batch = lb.Batch(boxes, storage=w["storage"], scheme=w["scheme"])
     tune = batch.autotune(2)                      # on the rest state, before the fields
     for k, b in enumerate(boxes):
@@ -402,7 +404,7 @@ def main_ours(args, rank, world, local):
             try:
                 vs = v.get("steps", 200)
                 if v["field"] == "batch":
-                    r = run_batch(v, vs, 3)
+                    r = run_batch(v, vs, 3, rank, world)
                     mlups = r["P"] * vs / (r["total_ms"] / 1e3) / 1e6
                     single = r["P"] / (r["single_box_ms_per_step"] / 1e3) / 1e6
                     variants[v["name"]] = {
