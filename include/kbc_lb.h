@@ -137,14 +137,22 @@ double lb_beta(const lb_ctx *ctx);
  * lb_set_populations). t >= 0. */
 lb_status lb_set_time(lb_ctx *ctx, int64_t t);
 
-/* Which step kernel runs. LB_KERNEL_STAGED stages the 27 source rows of each 128-node
- * x-segment in shared memory with asynchronous bulk copies (a pipelined persistent grid); it
- * needs nx * sizeof(stored value) to be a multiple of 16 bytes (else LB_ERR_UNSUPPORTED).
- * LB_KERNEL_DIRECT loads straight from global memory, one thread per node, any nx.
- * LB_KERNEL_AUTO (default) takes the staged kernel whenever it applies. All kernels produce
- * bit-identical populations. */
-enum { LB_KERNEL_AUTO = 0, LB_KERNEL_DIRECT = 1, LB_KERNEL_STAGED = 2 };
+/* Which step kernel runs. All of them produce bit-identical populations.
+ *   LB_KERNEL_PERSISTENT  a persistent grid walks 128-node row segments, one thread per node,
+ *                         loading from global memory; the bulk-copy engine prefetches into L2
+ *                         the source rows of segments a few items ahead (lb_set_prefetch) when
+ *                         rows are whole multiples of 16 bytes.
+ *   LB_KERNEL_STAGED      the same items with the 27 source rows staged in shared memory by
+ *                         asynchronous bulk copies in an mbarrier pipeline; needs
+ *                         nx * sizeof(stored value) % 16 == 0 (else LB_ERR_UNSUPPORTED).
+ *   LB_KERNEL_DIRECT      one thread per node over a full grid (lb_set_block), any nx.
+ *   LB_KERNEL_AUTO        (default) the persistent kernel. */
+enum { LB_KERNEL_AUTO = 0, LB_KERNEL_DIRECT = 1, LB_KERNEL_STAGED = 2, LB_KERNEL_PERSISTENT = 3 };
 lb_status lb_set_kernel(lb_ctx *ctx, int32_t kind);
+
+/* L2 prefetch distance of the persistent kernel, in work items per CTA (0 = off, at most 8;
+ * default 2). */
+lb_status lb_set_prefetch(lb_ctx *ctx, int32_t items_ahead);
 
 /* Launch shape of the direct kernel: threads per block along x (bx) and y (by), with
  * bx*by in {64, 128, 256, 512} (at most 256 for LB_F64) and bx a multiple of 32. */

@@ -19,6 +19,10 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
+#include "kbc_ops.h"
+
 namespace kbc {
 
 // ------------------------------------------------------------------ lattice constants
@@ -107,6 +111,11 @@ template <> struct Ar<float> {
   }
   static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
   static __device__ __forceinline__ float sqrt(float a) { return __fsqrt_rn(a); }
+  // hardware-approximate forms (about 2 ulp) where FP32 round-off is not the limit: the
+  // reciprocal weights of the entropic products, 1/rho, R = sqrt(1 + 3u^2) >= 1, and the
+  // ratio of eq:result21
+  static __device__ __forceinline__ float div_fast(float a, float b) { return __fdividef(a, b); }
+  static __device__ __forceinline__ float sqrt_fast(float a) { return __fmul_rn(a, rsqrtf(a)); }
 };
 template <> struct Ar<double> {
   static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
@@ -117,6 +126,9 @@ template <> struct Ar<double> {
   }
   static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
   static __device__ __forceinline__ double sqrt(double a) { return __dsqrt_rn(a); }
+  // FP64 keeps IEEE division and square root everywhere
+  static __device__ __forceinline__ double div_fast(double a, double b) { return __ddiv_rn(a, b); }
+  static __device__ __forceinline__ double sqrt_fast(double a) { return __dsqrt_rn(a); }
 };
 
 // One KBC collision on the shifted populations d[i] = f_i - W_i, in place (collision
@@ -164,14 +176,14 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, bool* 
   const R one = R(1), three = R(3);
   const R drho = D000;
   const R rho = O::add(one, drho);
-  const R ir = O::div(one, rho);
+  const R ir = O::div_fast(one, rho);
   const R ux = O::mul(D100, ir), uy = O::mul(D010, ir), uz = O::mul(D001, ir);
 
   // ---- per-axis equilibrium factors (listing step 2): e = R - 1 = 3u^2 / (1 + R)
   auto axis_e = [&](R u) {
     const R u3 = O::mul(three, O::mul(u, u));
-    const R Rr = O::sqrt(O::add(one, u3));
-    return O::div(u3, O::add(one, Rr));
+    const R Rr = O::sqrt_fast(O::add(one, u3));
+    return O::div_fast(u3, O::add(one, Rr));
   };
   const R ex = axis_e(ux), ey = axis_e(uy), ez = axis_e(uz);
   const R c23 = R(2.0 / 3.0), c13 = R(1.0 / 3.0);
@@ -247,7 +259,7 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, bool* 
     const R p1 = O::mul(c23, O::add(one, e[1]));
     const R p2 = O::mul(c16, O::add(one, e[2]));
     const R p12 = O::mul(p1, p2);
-    const R q = O::div(one, O::mul(p0, p12));   // one division for three reciprocals
+    const R q = O::div_fast(one, O::mul(p0, p12));   // one division for three reciprocals
     const R qp0 = O::mul(q, p0);
     r[0] = O::mul(p12, q);
     r[1] = O::mul(p2, qp0);
@@ -263,6 +275,12 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, bool* 
   const R nb2 = R(-cp.two_beta);
   R dh[27];
   R num = R(0), den = R(0);
+  // (1 + gx)(1 + fy) - 1 for the 9 (a, b) pairs, shared by the three z levels
+  R Pab[9];
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Pab[a + 3 * b] = O::fma(gx[a], fy[b], O::add(gx[a], fy[b]));
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     R cn = R(0), cd = R(0);
@@ -273,7 +291,7 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, bool* 
       for (int a = 0; a < 3; ++a) {
         const int i = a + 3 * b + 9 * c;
         // (f_eq_i - W_i)/W_i = (1 + gx)(1 + fy)(1 + fz) - 1 without cancellation
-        const R P = O::fma(gx[a], fy[b], O::add(gx[a], fy[b]));
+        const R P = Pab[a + 3 * b];
         const R G = O::fma(P, fz[c], O::add(P, fz[c]));
         const R dsi = ds_of(a - 1, b - 1, c - 1);
         const R dhi = O::sub(O::fma(R(-wgt(i)), G, d[i]), dsi);
@@ -299,7 +317,7 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, bool* 
   } else if (cp.gamma_mode == GAMMA_RLB) {
     gamma = ib;
   } else if (den > Guard<R>::den) {
-    gamma = O::fma(-O::sub(R(2), ib), O::div(num, den), ib);
+    gamma = O::fma(-O::sub(R(2), ib), O::div_fast(num, den), ib);
   } else if (den == den) {
     gamma = R(2);
     *guarded = true;
@@ -396,5 +414,40 @@ template <int I, int N> struct Unroll {
 template <int N> struct Unroll<N, N> {
   template <typename F> __device__ __forceinline__ static void run(F&&) {}
 };
+
+// ------------------------------------------------------------------ the fused node update
+// Loads f(x, t) of node (x, y, z) by the pattern of MODE, collides, stores f'(x) where
+// f(t+1) expects it. src and dst are the same buffer in the AA modes.
+template <typename S, int MODE, bool RECORD>
+__device__ __forceinline__ void node_update(const S* src, S* dst, const Geo& g, uint32_t x,
+                                            uint32_t y, uint32_t z, const CollideParams& cp,
+                                            float* gamma_out, StepCounters* ctr) {
+  using C = Codec<S>;
+  using R = typename C::R;
+  using Pat = Pattern<MODE>;
+  Nbr nb;
+  nb.init(g, x, y, z);
+  R d[27];
+  Unroll<0, 27>::run([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    const S* p = src + (uint64_t)Pat::load_plane(I) * g.P + nb.template at<I, Pat::load_shift>();
+    if constexpr (MODE == MODE_PULL) {
+      d[I] = C::template load_ro<I>(p);
+    } else {
+      d[I] = C::template load<I>(p);
+    }
+  });
+  bool guarded;
+  const R gamma = collide<R>(d, cp, &guarded);
+  Unroll<0, 27>::run([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    S* p = dst + (uint64_t)Pat::store_plane(I) * g.P + nb.template at<I, Pat::store_shift>();
+    C::template store<I>(p, d[I]);
+  });
+  if constexpr (RECORD) {
+    gamma_out[nb.ox[1] + nb.oy[1] + nb.oz[1]] = (float)gamma;
+    if (guarded) atomicAdd(&ctr->guarded, 1ull);
+  }
+}
 
 }  // namespace kbc

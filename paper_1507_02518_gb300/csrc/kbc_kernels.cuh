@@ -13,41 +13,6 @@
 
 namespace kbc {
 
-// ------------------------------------------------------------------ the fused node update
-// Loads f(x, t) of node (x, y, z) by the pattern of MODE, collides, stores f'(x) where
-// f(t+1) expects it. src and dst are the same buffer in the AA modes.
-template <typename S, int MODE, bool RECORD>
-__device__ __forceinline__ void node_update(const S* src, S* dst, const Geo& g, uint32_t x,
-                                            uint32_t y, uint32_t z, const CollideParams& cp,
-                                            float* gamma_out, StepCounters* ctr) {
-  using C = Codec<S>;
-  using R = typename C::R;
-  using Pat = Pattern<MODE>;
-  Nbr nb;
-  nb.init(g, x, y, z);
-  R d[27];
-  Unroll<0, 27>::run([&](auto ic) {
-    constexpr int I = decltype(ic)::value;
-    const S* p = src + (uint64_t)Pat::load_plane(I) * g.P + nb.template at<I, Pat::load_shift>();
-    if constexpr (MODE == MODE_PULL) {
-      d[I] = C::template load_ro<I>(p);
-    } else {
-      d[I] = C::template load<I>(p);
-    }
-  });
-  bool guarded;
-  const R gamma = collide<R>(d, cp, &guarded);
-  Unroll<0, 27>::run([&](auto ic) {
-    constexpr int I = decltype(ic)::value;
-    S* p = dst + (uint64_t)Pat::store_plane(I) * g.P + nb.template at<I, Pat::store_shift>();
-    C::template store<I>(p, d[I]);
-  });
-  if constexpr (RECORD) {
-    gamma_out[nb.ox[1] + nb.oy[1] + nb.oz[1]] = (float)gamma;
-    if (guarded) atomicAdd(&ctr->guarded, 1ull);
-  }
-}
-
 // FP64 arithmetic needs more than 128 registers per thread: cap its blocks at 256 threads
 template <typename S> struct MaxThreads { static constexpr int value = 512; };
 template <> struct MaxThreads<double> { static constexpr int value = 256; };
@@ -374,10 +339,11 @@ template <typename S, int MODE, bool RECORD>
 static cudaError_t launch_step(const BoxView& b, const S* src, S* dst, const Geo& g,
                                const CollideParams& cp, const StepOpts& o, StepCounters* ctr,
                                cudaStream_t st) {
-  const bool staged = o.kernel == KERNEL_STAGED ||
-                      (o.kernel == KERNEL_AUTO && staged_supported<S>(b.nx));
-  if (staged)
+  if (o.kernel == KERNEL_STAGED)
     return launch_staged<S, MODE, RECORD>(src, dst, g, cp, b.gamma, ctr, o.budget, o.stall, st);
+  if (o.kernel == KERNEL_PERSISTENT || o.kernel == KERNEL_AUTO)
+    return launch_persistent<S, MODE, RECORD>(src, dst, g, cp, b.gamma, ctr,
+                                              (uint32_t)o.prefetch, st);
   const dim3 block(o.bx, o.by, 1);
   const dim3 grid((b.nx + o.bx - 1) / o.bx, (b.ny + o.by - 1) / o.by, b.nz);
   step_kernel<S, MODE, RECORD><<<grid, block, 0, st>>>(src, dst, g, cp, b.gamma, ctr);

@@ -25,10 +25,11 @@ struct StepCounters {
 };
 
 // kernel choice and test hooks of one step launch
-enum { KERNEL_AUTO = 0, KERNEL_DIRECT = 1, KERNEL_STAGED = 2 };
+enum { KERNEL_AUTO = 0, KERNEL_DIRECT = 1, KERNEL_STAGED = 2, KERNEL_PERSISTENT = 3 };
 struct StepOpts {
   int bx, by;                 // block of the direct kernel
   int kernel;                 // KERNEL_*
+  int prefetch;               // L2 prefetch distance of the persistent kernel (items)
   unsigned long long budget;  // wait budget (SM cycles) of the staged kernel
   int stall;                  // test hook: the staged kernel issues no copies
 };

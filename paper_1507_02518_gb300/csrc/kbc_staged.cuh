@@ -206,6 +206,88 @@ __global__ void __launch_bounds__(kSeg, StagedCfg<S>::min_blocks) staged_step_ke
   }
 }
 
+// ------------------------------------------------------------------ persistent + L2 prefetch
+// The same 128-node row-segment items, walked by a persistent grid without shared memory:
+// each thread loads its node's 27 values straight from global memory, while lanes 0..26 of
+// warp 0 ask the bulk-copy engine to prefetch into L2 the 27 source row segments of the item
+// `prefetch` steps ahead (cp.async.bulk.prefetch.L2: no destination, no barrier, no wait).
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
+template <typename S> struct PersistCfg { static constexpr int min_blocks = 4; };
+template <> struct PersistCfg<double> { static constexpr int min_blocks = 2; };
+
+struct PersistArgs {
+  uint32_t nseg, nitems;
+  uint32_t prefetch;  // items ahead (0: off; needs rows of whole 16-byte multiples)
+};
+
+template <typename S, int MODE>
+__device__ __forceinline__ void prefetch_item(const S* src, const Geo& g, const PersistArgs& a,
+                                              uint32_t item, int lane) {
+  using Pat = Pattern<MODE>;
+  const uint32_t seg = item % a.nseg;
+  const uint32_t row = item / a.nseg;
+  const uint32_t y = row % g.ny, z = row / g.ny;
+  const uint32_t x0 = seg * kSeg;
+  const uint32_t cnt = min((uint32_t)kSeg, g.nx - x0);
+  const int i = lane;
+  const int sy = Pat::load_shift * cy(i), sz = Pat::load_shift * cz(i);
+  const uint32_t ys = sy < 0 ? (y == 0 ? g.ny - 1 : y - 1) : (sy > 0 ? (y + 1 == g.ny ? 0 : y + 1) : y);
+  const uint32_t zs = sz < 0 ? (z == 0 ? g.nz - 1 : z - 1) : (sz > 0 ? (z + 1 == g.nz ? 0 : z + 1) : z);
+  const S* rowp = src + (uint64_t)Pat::load_plane(i) * g.P + ((uint64_t)zs * g.ny + ys) * g.nx;
+  bulk_prefetch_l2(rowp + x0, cnt * (uint32_t)sizeof(S));
+}
+
+template <typename S, int MODE, bool RECORD>
+__global__ void __launch_bounds__(kSeg, PersistCfg<S>::min_blocks)
+    persistent_step_kernel(const S* src, S* dst, Geo g, CollideParams cp, float* gamma_out,
+                           StepCounters* ctr, PersistArgs a) {
+  const int tid = threadIdx.x;
+  if (a.prefetch && tid < 27)
+    for (uint32_t d = 0; d < a.prefetch; ++d) {
+      const uint32_t item = blockIdx.x + d * gridDim.x;
+      if (item < a.nitems) prefetch_item<S, MODE>(src, g, a, item, tid);
+    }
+  for (uint32_t item = blockIdx.x; item < a.nitems; item += gridDim.x) {
+    if (a.prefetch && tid < 27) {
+      const uint32_t ahead = item + a.prefetch * gridDim.x;
+      if (ahead < a.nitems) prefetch_item<S, MODE>(src, g, a, ahead, tid);
+    }
+    const uint32_t seg = item % a.nseg;
+    const uint32_t row = item / a.nseg;
+    const uint32_t y = row % g.ny, z = row / g.ny;
+    const uint32_t x = seg * kSeg + tid;
+    if (x < g.nx) node_update<S, MODE, RECORD>(src, dst, g, x, y, z, cp, gamma_out, ctr);
+  }
+}
+
+template <typename S, int MODE, bool RECORD>
+cudaError_t launch_persistent(const S* src, S* dst, const Geo& g, const CollideParams& cp,
+                              float* gamma_out, StepCounters* ctr, uint32_t prefetch,
+                              cudaStream_t st) {
+  static int blocks_per_sm = 0;
+  static int sms = 0;
+  auto kern = persistent_step_kernel<S, MODE, RECORD>;
+  if (blocks_per_sm == 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, kSeg, 0);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+  }
+  PersistArgs a;
+  a.nseg = (g.nx + kSeg - 1) / kSeg;
+  a.nitems = a.nseg * g.ny * g.nz;
+  a.prefetch = (((uint64_t)g.nx * sizeof(S)) % 16 == 0) ? prefetch : 0;
+  const uint32_t cap = (uint32_t)(sms * blocks_per_sm);
+  const uint32_t grid = a.nitems < cap ? a.nitems : cap;
+  kern<<<grid, kSeg, 0, st>>>(src, dst, g, cp, gamma_out, ctr, a);
+  return cudaGetLastError();
+}
+
 // true if the staged kernel can run this box: rows are whole multiples of 16 bytes
 template <typename S> inline bool staged_supported(uint32_t nx) {
   return ((uint64_t)nx * sizeof(S)) % 16 == 0;

@@ -143,6 +143,7 @@ struct lb_ctx {
   uint64_t stage_nodes = 0;
   int bx = 128, by = 1;
   int kernel = kbc::KERNEL_AUTO;
+  int prefetch = 2;
   unsigned long long wait_budget = 2000000000ull;  // about 1 s at the SM clock
   int stall = 0;
   bool gamma_valid = false;
@@ -237,6 +238,7 @@ kbc::StepOpts step_opts(const lb_ctx* c) {
   o.bx = c->bx;
   o.by = c->by;
   o.kernel = c->kernel;
+  o.prefetch = c->prefetch;
   o.budget = c->wait_budget;
   o.stall = c->stall;
   return o;
@@ -486,8 +488,9 @@ lb_status lb_set_time(lb_ctx* c, int64_t t) {
 
 lb_status lb_set_kernel(lb_ctx* c, int32_t kind) {
   if (!c) return LB_ERR_INVALID_ARG;
-  if (kind != LB_KERNEL_AUTO && kind != LB_KERNEL_DIRECT && kind != LB_KERNEL_STAGED)
-    return fail(c, LB_ERR_INVALID_ARG, "kind must be LB_KERNEL_AUTO, _DIRECT or _STAGED");
+  if (kind < LB_KERNEL_AUTO || kind > LB_KERNEL_PERSISTENT)
+    return fail(c, LB_ERR_INVALID_ARG, "kind must be LB_KERNEL_AUTO, _DIRECT, _STAGED or "
+                                       "_PERSISTENT");
   if (kind == LB_KERNEL_STAGED) {
     bool ok = false;
     dispatch(c, [&](auto ops) {
@@ -499,6 +502,14 @@ lb_status lb_set_kernel(lb_ctx* c, int32_t kind) {
                                          "multiple of 16 bytes");
   }
   c->kernel = kind;
+  return LB_OK;
+}
+
+lb_status lb_set_prefetch(lb_ctx* c, int32_t items_ahead) {
+  if (!c) return LB_ERR_INVALID_ARG;
+  if (items_ahead < 0 || items_ahead > 8)
+    return fail(c, LB_ERR_INVALID_ARG, "items_ahead must be in [0, 8]");
+  c->prefetch = items_ahead;
   return LB_OK;
 }
 

@@ -22,8 +22,9 @@ LB_S_D, LB_S_DT, LB_S_DQ, LB_S_DTQ = range(4)
 LB_GAMMA_ESTIMATE, LB_GAMMA_LBGK, LB_GAMMA_RLB = range(3)
 LB_F64, LB_F32, LB_F16 = range(3)
 LB_PULL, LB_AA = range(2)
-LB_KERNEL_AUTO, LB_KERNEL_DIRECT, LB_KERNEL_STAGED = range(3)
-KERNEL = {"auto": LB_KERNEL_AUTO, "direct": LB_KERNEL_DIRECT, "staged": LB_KERNEL_STAGED}
+LB_KERNEL_AUTO, LB_KERNEL_DIRECT, LB_KERNEL_STAGED, LB_KERNEL_PERSISTENT = range(4)
+KERNEL = {"auto": LB_KERNEL_AUTO, "direct": LB_KERNEL_DIRECT, "staged": LB_KERNEL_STAGED,
+          "persistent": LB_KERNEL_PERSISTENT}
 
 STORAGE = {"f64": LB_F64, "f32": LB_F32, "f16": LB_F16}
 SCHEME = {"pull": LB_PULL, "aa": LB_AA}
@@ -62,7 +63,7 @@ _lock = threading.Lock()
 SYMBOLS = ["lb_required_bytes", "lb_create", "lb_destroy", "lb_last_error", "lb_init_field",
            "lb_step", "lb_moments", "lb_diagnostics", "lb_get_populations",
            "lb_set_populations", "lb_time", "lb_beta", "lb_set_time", "lb_set_block",
-           "lb_set_kernel", "lb_set_wait_budget",
+           "lb_set_kernel", "lb_set_prefetch", "lb_set_wait_budget",
            "lb_batch_required_bytes", "lb_batch_create", "lb_batch_destroy",
            "lb_batch_last_error", "lb_batch_box", "lb_batch_step", "lb_batch_diagnostics",
            "lb_batch_autotune", "lb_batch_set_tile"]
@@ -116,6 +117,8 @@ def load(path: str = LIB_PATH):
         L.lb_set_block.argtypes = [vp, i32, i32]
         L.lb_set_kernel.restype = i32
         L.lb_set_kernel.argtypes = [vp, i32]
+        L.lb_set_prefetch.restype = i32
+        L.lb_set_prefetch.argtypes = [vp, i32]
         L.lb_set_wait_budget.restype = i32
         L.lb_set_wait_budget.argtypes = [vp, ctypes.c_uint64, i32]
         L.lb_batch_required_bytes.restype = ctypes.c_size_t
@@ -229,6 +232,10 @@ def lb_set_block(ctx, bx: int, by: int):
 
 def lb_set_kernel(ctx, kind):
     _check(load().lb_set_kernel(ctx, KERNEL[kind] if isinstance(kind, str) else int(kind)), ctx)
+
+
+def lb_set_prefetch(ctx, items_ahead: int):
+    _check(load().lb_set_prefetch(ctx, int(items_ahead)), ctx)
 
 
 def lb_set_wait_budget(ctx, cycles: int, stall_copies: bool = False):

@@ -140,6 +140,7 @@ def test_fp64_matches_oracle_variants(kbc, variant, gamma):
 def test_fp64_launch_shapes_agree(kbc, bx, by):
     f0 = seeded_state(37, 11, 5)
     lat = lattice((37, 11, 5), storage="f64", scheme="pull")
+    lat.set_kernel("direct")
     lat.set_block(bx, by)
     lat.set_populations(f0)
     lat.step(3)
@@ -165,21 +166,23 @@ def test_pull_and_aa_are_bitwise_identical(kbc, storage, steps):
 @pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
 @pytest.mark.parametrize("scheme", ["pull", "aa"])
 @pytest.mark.parametrize("shape", [(200, 3, 4), (256, 5, 3), (8, 6, 5)])
-def test_staged_and_direct_kernels_are_bitwise_identical(kbc, storage, scheme, shape):
-    """The shared-memory staged kernel (bulk copies, several x-segments, ragged last segment,
-    periodic wrap inside the staged rows) against the direct kernel."""
+def test_all_step_kernels_are_bitwise_identical(kbc, storage, scheme, shape):
+    """Direct, shared-memory staged (bulk copies, several x-segments, ragged last segment,
+    periodic wrap inside the staged rows) and persistent (with and without L2 prefetch)."""
     f0 = seeded_state(*shape, seed=9)
     out = []
-    for kind in ("direct", "staged"):
+    for kind, pf in (("direct", 2), ("staged", 2), ("persistent", 0), ("persistent", 3)):
         lat = lattice(shape, storage=storage, scheme=scheme)
         lat.set_kernel(kind)
+        lb.lb_set_prefetch(lat.ctx, pf)
         lat.set_populations(f0)
         lat.step(5)
         out.append(lat.get_populations())
-    assert np.array_equal(out[0], out[1])
+    for o in out[1:]:
+        assert np.array_equal(out[0], o)
     ref, _, _ = oracle.run(f0, 5, oracle.beta(1e-3))
     tol = {"f64": FP64_TOL, "f32": 1e-6, "f16": 2e-3}[storage]
-    assert np.max(np.abs(out[1] - ref)) <= tol
+    assert np.max(np.abs(out[0] - ref)) <= tol
 
 
 def test_staged_kernel_rejects_unaligned_rows(kbc):
