@@ -138,6 +138,8 @@ double lb_beta(const lb_ctx *ctx);
 lb_status lb_set_time(lb_ctx *ctx, int64_t t);
 
 /* Which step kernel runs. All of them produce bit-identical populations.
+ *   LB_KERNEL_PACKED      two nodes per thread, (x, x+32) of one row, the collision on
+ *                         packed FP32x2 instructions; LB_F32 / LB_F16 only.
  *   LB_KERNEL_PERSISTENT  a persistent grid walks 128-node row segments, one thread per node,
  *                         loading from global memory; the bulk-copy engine prefetches into L2
  *                         the source rows of segments a few items ahead (lb_set_prefetch) when
@@ -146,8 +148,14 @@ lb_status lb_set_time(lb_ctx *ctx, int64_t t);
  *                         asynchronous bulk copies in an mbarrier pipeline; needs
  *                         nx * sizeof(stored value) % 16 == 0 (else LB_ERR_UNSUPPORTED).
  *   LB_KERNEL_DIRECT      one thread per node over a full grid (lb_set_block), any nx.
- *   LB_KERNEL_AUTO        (default) the persistent kernel. */
-enum { LB_KERNEL_AUTO = 0, LB_KERNEL_DIRECT = 1, LB_KERNEL_STAGED = 2, LB_KERNEL_PERSISTENT = 3 };
+ *   LB_KERNEL_AUTO        (default) packed for FP32 arithmetic, direct for LB_F64. */
+enum {
+  LB_KERNEL_AUTO = 0,
+  LB_KERNEL_DIRECT = 1,
+  LB_KERNEL_STAGED = 2,
+  LB_KERNEL_PERSISTENT = 3,
+  LB_KERNEL_PACKED = 4
+};
 lb_status lb_set_kernel(lb_ctx *ctx, int32_t kind);
 
 /* L2 prefetch distance of the persistent kernel, in work items per CTA (0 = off, at most 8;

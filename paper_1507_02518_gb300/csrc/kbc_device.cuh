@@ -100,42 +100,78 @@ struct CollideParams {
 
 // Explicitly rounded arithmetic. Every operation of the collision goes through these, so
 // the compiler neither contracts nor reorders anything: all kernels that inline collide()
-// (pull, AA even/odd, batched) produce bit-identical populations from identical inputs.
+// (pull, AA even/odd, batched, one or two nodes per thread) produce bit-identical populations
+// from identical inputs. Ar<float2> holds two nodes and uses the packed FP32x2 instructions of
+// sm_100+ (each lane is rounded exactly like the scalar operation).
 template <typename R> struct Ar;
 template <> struct Ar<float> {
+  using Scalar = float;
+  static constexpr int lanes = 1;
+  static __device__ __forceinline__ float c(double v) { return (float)v; }
+  static __device__ __forceinline__ float neg(float a) { return -a; }
   static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
   static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
   static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
   static __device__ __forceinline__ float fma(float a, float b, float c) {
     return __fmaf_rn(a, b, c);
   }
-  static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
-  static __device__ __forceinline__ float sqrt(float a) { return __fsqrt_rn(a); }
   // hardware-approximate forms (about 2 ulp) where FP32 round-off is not the limit: the
   // reciprocal weights of the entropic products, 1/rho, R = sqrt(1 + 3u^2) >= 1, and the
   // ratio of eq:result21
   static __device__ __forceinline__ float div_fast(float a, float b) { return __fdividef(a, b); }
   static __device__ __forceinline__ float sqrt_fast(float a) { return __fmul_rn(a, rsqrtf(a)); }
+  static __device__ __forceinline__ float lane(float a, int) { return a; }
+  static __device__ __forceinline__ void set_lane(float& a, int, float v) { a = v; }
+};
+template <> struct Ar<float2> {
+  using Scalar = float;
+  static constexpr int lanes = 2;
+  static __device__ __forceinline__ float2 c(double v) { return make_float2((float)v, (float)v); }
+  static __device__ __forceinline__ float2 neg(float2 a) { return make_float2(-a.x, -a.y); }
+  static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+  static __device__ __forceinline__ float2 sub(float2 a, float2 b) {
+    return __fadd2_rn(a, neg(b));
+  }
+  static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+  static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) {
+    return __ffma2_rn(a, b, c);
+  }
+  static __device__ __forceinline__ float2 div_fast(float2 a, float2 b) {
+    return make_float2(__fdividef(a.x, b.x), __fdividef(a.y, b.y));
+  }
+  static __device__ __forceinline__ float2 sqrt_fast(float2 a) {
+    return make_float2(__fmul_rn(a.x, rsqrtf(a.x)), __fmul_rn(a.y, rsqrtf(a.y)));
+  }
+  static __device__ __forceinline__ float lane(float2 a, int k) { return k ? a.y : a.x; }
+  static __device__ __forceinline__ void set_lane(float2& a, int k, float v) {
+    if (k) a.y = v; else a.x = v;
+  }
 };
 template <> struct Ar<double> {
+  using Scalar = double;
+  static constexpr int lanes = 1;
+  static __device__ __forceinline__ double c(double v) { return v; }
+  static __device__ __forceinline__ double neg(double a) { return -a; }
   static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
   static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
   static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
   static __device__ __forceinline__ double fma(double a, double b, double c) {
     return __fma_rn(a, b, c);
   }
-  static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
-  static __device__ __forceinline__ double sqrt(double a) { return __dsqrt_rn(a); }
   // FP64 keeps IEEE division and square root everywhere
   static __device__ __forceinline__ double div_fast(double a, double b) { return __ddiv_rn(a, b); }
   static __device__ __forceinline__ double sqrt_fast(double a) { return __dsqrt_rn(a); }
+  static __device__ __forceinline__ double lane(double a, int) { return a; }
+  static __device__ __forceinline__ void set_lane(double& a, int, double v) { a = v; }
 };
 
 // One KBC collision on the shifted populations d[i] = f_i - W_i, in place (collision
-// listing of Sec. KBC). Returns gamma; *guarded is set when <dh|dh> fell under the guard.
+// listing of Sec. KBC); R holds one node (float, double) or two (float2). Returns gamma;
+// bit k of *guarded is set when lane k's <dh|dh> fell under the guard.
 template <typename R>
-__device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, bool* guarded) {
+__device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, int* guarded) {
   using O = Ar<R>;
+  using T = typename O::Scalar;
   // ---- natural moments of delta by a factorised x -> y -> z reduction (eq:natmoments)
   // row r = (vy+1) + 3(vz+1); X0 = sum over vx, X1 = sum vx, X2 = sum vx^2
   R X0[9], X1[9], X2[9];
@@ -173,7 +209,7 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, bool* 
   const R D210 = zsum(Y21);
 
   // ---- conserved quantities (listing step 1); sum W = 1, sum W v = 0
-  const R one = R(1), three = R(3);
+  const R one = O::c(1.0), three = O::c(3.0);
   const R drho = D000;
   const R rho = O::add(one, drho);
   const R ir = O::div_fast(one, rho);
@@ -186,30 +222,31 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, bool* 
     return O::div_fast(u3, O::add(one, Rr));
   };
   const R ex = axis_e(ux), ey = axis_e(uy), ez = axis_e(uz);
-  const R c23 = R(2.0 / 3.0), c13 = R(1.0 / 3.0);
+  const R c23 = O::c(2.0 / 3.0), c13 = O::c(1.0 / 3.0);
   const R m2x = O::fma(c23, ex, c13);  // m_2(u) = (2R - 1)/3
   const R m2y = O::fma(c23, ey, c13);
   const R m2z = O::fma(c23, ez, c13);
 
   // ---- rho-scaled moment deviations rho (M - M_eq) (listing steps 3-4)
-  const R rc23 = O::mul(rho, c23);
-  const R nd3 = O::mul(drho, -c13);
-  const R A200 = O::fma(-rc23, ex, O::add(D200, nd3));
-  const R A020 = O::fma(-rc23, ey, O::add(D020, nd3));
-  const R A002 = O::fma(-rc23, ez, O::add(D002, nd3));
+  const R nrc23 = O::neg(O::mul(rho, c23));
+  const R nd3 = O::mul(drho, O::c(-1.0 / 3.0));
+  const R A200 = O::fma(nrc23, ex, O::add(D200, nd3));
+  const R A020 = O::fma(nrc23, ey, O::add(D020, nd3));
+  const R A002 = O::fma(nrc23, ez, O::add(D002, nd3));
   const R ANxz = O::sub(A200, A002), ANyz = O::sub(A020, A002);
-  const R AT = cp.with_t ? O::add(O::add(A200, A020), A002) : R(0);
-  const R APxy = O::fma(-D100, uy, D110), APxz = O::fma(-D100, uz, D101);
-  const R APyz = O::fma(-D010, uz, D011);
-  const R qs = cp.with_q ? R(1) : R(0);
-  const R AQxyy = O::mul(qs, O::fma(-D100, m2y, D120)), AQxzz = O::mul(qs, O::fma(-D100, m2z, D102));
-  const R AQxxy = O::mul(qs, O::fma(-D010, m2x, D210)), AQyzz = O::mul(qs, O::fma(-D010, m2z, D012));
-  const R AQxxz = O::mul(qs, O::fma(-D001, m2x, D201)), AQyyz = O::mul(qs, O::fma(-D001, m2y, D021));
-  const R AQxyz = O::mul(qs, O::fma(-O::mul(D100, uy), uz, D111));
+  const R AT = cp.with_t ? O::add(O::add(A200, A020), A002) : O::c(0.0);
+  const R nD100 = O::neg(D100), nD010 = O::neg(D010), nD001 = O::neg(D001);
+  const R APxy = O::fma(nD100, uy, D110), APxz = O::fma(nD100, uz, D101);
+  const R APyz = O::fma(nD010, uz, D011);
+  const R qs = O::c(cp.with_q ? 1.0 : 0.0);
+  const R AQxyy = O::mul(qs, O::fma(nD100, m2y, D120)), AQxzz = O::mul(qs, O::fma(nD100, m2z, D102));
+  const R AQxxy = O::mul(qs, O::fma(nD010, m2x, D210)), AQyzz = O::mul(qs, O::fma(nD010, m2z, D012));
+  const R AQxxz = O::mul(qs, O::fma(nD001, m2x, D201)), AQyyz = O::mul(qs, O::fma(nD001, m2y, D021));
+  const R AQxyz = O::mul(qs, O::fma(O::neg(O::mul(D100, uy)), uz, D111));
 
   // Table 1 per velocity class: ds = d + t + q evaluated on the deviations
-  const R c16 = R(1.0 / 6.0), half = R(0.5), quarter = R(0.25);
-  const R s0 = -AT;
+  const R c16 = O::c(1.0 / 6.0), half = O::c(0.5), quarter = O::c(0.25);
+  const R s0 = O::neg(AT);
   const R Fx = O::mul(O::add(O::sub(O::add(ANxz, ANxz), ANyz), AT), c16);
   const R Fy = O::mul(O::add(O::sub(O::add(ANyz, ANyz), ANxz), AT), c16);
   const R Fz = O::mul(O::sub(O::sub(AT, ANxz), ANyz), c16);
@@ -221,8 +258,8 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, bool* 
   const R Qxxy4 = O::mul(quarter, AQxxy), Qxyy4 = O::mul(quarter, AQxyy);
   const R Qxxz4 = O::mul(quarter, AQxxz), Qxzz4 = O::mul(quarter, AQxzz);
   const R Qyyz4 = O::mul(quarter, AQyyz), Qyzz4 = O::mul(quarter, AQyzz);
-  const R Qxyz8 = O::mul(R(0.125), AQxyz);
-  auto sg = [](int s, R v) { return s > 0 ? v : -v; };
+  const R Qxyz8 = O::mul(O::c(0.125), AQxyz);
+  auto sg = [](int s, R v) { return s > 0 ? v : O::neg(v); };
   // (s1 P) + (s2 Q1) + (s3 Q2) for an edge class; signs are compile-time after unrolling
   auto edge = [&](int sp, R P4, int s1, R Q1, int s2, R Q2) {
     return O::add(O::add(sg(sp, P4), sg(s1, Q1)), sg(s2, Q2));
@@ -245,14 +282,12 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, bool* 
 
   // equilibrium factors: rho phi_x(a) = W_a (1 + gx_a), phi_y(b) = W_b (1 + fy_b), ...
   // with e_0 = -e, e_{+-1} = 2e +- 3u; the x factor carries rho: gx = drho + rho e_x
-  const R two = R(2);
   const R tex = O::add(ex, ex), tey = O::add(ey, ey), tez = O::add(ez, ez);
   const R ux3 = O::mul(three, ux), uy3 = O::mul(three, uy), uz3 = O::mul(three, uz);
-  const R gx[3] = {O::fma(rho, O::sub(tex, ux3), drho), O::fma(-rho, ex, drho),
+  const R gx[3] = {O::fma(rho, O::sub(tex, ux3), drho), O::fma(O::neg(rho), ex, drho),
                    O::fma(rho, O::add(tex, ux3), drho)};
-  const R fy[3] = {O::sub(tey, uy3), -ey, O::add(tey, uy3)};
-  const R fz[3] = {O::sub(tez, uz3), -ez, O::add(tez, uz3)};
-  (void)two;
+  const R fy[3] = {O::sub(tey, uy3), O::neg(ey), O::add(tey, uy3)};
+  const R fz[3] = {O::sub(tez, uz3), O::neg(ez), O::add(tez, uz3)};
   // reciprocal weights of the entropic scalar product, 1/f_eq_i = rx[a] ry[b] rz[c]
   auto recip_axis = [&](const R (&e)[3], R (&r)[3]) {
     const R p0 = O::mul(c16, O::add(one, e[0]));
@@ -272,9 +307,9 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, bool* 
 
   // ---- dh, the two entropic products, and the part of the relaxation known before gamma
   // (listing steps 5-6): d <- d - 2 beta ds, dh kept for the gamma-dependent part
-  const R nb2 = R(-cp.two_beta);
+  const R nb2 = O::c(-cp.two_beta);
   R dh[27];
-  R num = R(0), den = R(0);
+  R num = O::c(0.0), den = O::c(0.0);
   // (1 + gx)(1 + fy) - 1 for the 9 (a, b) pairs, shared by the three z levels
   R Pab[9];
 #pragma unroll
@@ -283,10 +318,10 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, bool* 
     for (int a = 0; a < 3; ++a) Pab[a + 3 * b] = O::fma(gx[a], fy[b], O::add(gx[a], fy[b]));
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    R cn = R(0), cd = R(0);
+    R cn = O::c(0.0), cd = O::c(0.0);
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      R rn = R(0), rd = R(0);
+      R rn = O::c(0.0), rd = O::c(0.0);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const int i = a + 3 * b + 9 * c;
@@ -294,7 +329,7 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, bool* 
         const R P = Pab[a + 3 * b];
         const R G = O::fma(P, fz[c], O::add(P, fz[c]));
         const R dsi = ds_of(a - 1, b - 1, c - 1);
-        const R dhi = O::sub(O::fma(R(-wgt(i)), G, d[i]), dsi);
+        const R dhi = O::sub(O::fma(O::c(-wgt(i)), G, d[i]), dsi);
         const R t1 = O::mul(rx[a], dhi);
         rn = O::fma(t1, dsi, rn);
         rd = O::fma(t1, dhi, rd);
@@ -309,22 +344,29 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, bool* 
   }
 
   // ---- stabilizer (eq:result21) and the rest of the relaxation (listing step 7)
-  const R ib = R(cp.inv_beta);
-  R gamma;
-  *guarded = false;
-  if (cp.gamma_mode == GAMMA_LBGK) {
-    gamma = R(2);
-  } else if (cp.gamma_mode == GAMMA_RLB) {
-    gamma = ib;
-  } else if (den > Guard<R>::den) {
-    gamma = O::fma(-O::sub(R(2), ib), O::div_fast(num, den), ib);
-  } else if (den == den) {
-    gamma = R(2);
-    *guarded = true;
-  } else {
-    gamma = den;  // NaN propagates to the populations and to the diagnostics
+  const T ib = (T)cp.inv_beta;
+  R gamma = O::c(0.0);
+  int gmask = 0;
+#pragma unroll
+  for (int k = 0; k < O::lanes; ++k) {
+    const T nk = O::lane(num, k), dk = O::lane(den, k);
+    T gk;
+    if (cp.gamma_mode == GAMMA_LBGK) {
+      gk = T(2);
+    } else if (cp.gamma_mode == GAMMA_RLB) {
+      gk = ib;
+    } else if (dk > Guard<T>::den) {
+      gk = Ar<T>::fma(-Ar<T>::sub(T(2), ib), Ar<T>::div_fast(nk, dk), ib);
+    } else if (dk == dk) {
+      gk = T(2);
+      gmask |= 1 << k;
+    } else {
+      gk = dk;  // NaN propagates to the populations and to the diagnostics
+    }
+    O::set_lane(gamma, k, gk);
   }
-  const R nbg = -O::mul(R(cp.beta), gamma);
+  *guarded = gmask;
+  const R nbg = O::neg(O::mul(O::c(cp.beta), gamma));
 #pragma unroll
   for (int i = 0; i < 27; ++i) d[i] = O::fma(nbg, dh[i], d[i]);
   return gamma;
@@ -437,7 +479,7 @@ __device__ __forceinline__ void node_update(const S* src, S* dst, const Geo& g, 
       d[I] = C::template load<I>(p);
     }
   });
-  bool guarded;
+  int guarded;
   const R gamma = collide<R>(d, cp, &guarded);
   Unroll<0, 27>::run([&](auto ic) {
     constexpr int I = decltype(ic)::value;
@@ -447,6 +489,51 @@ __device__ __forceinline__ void node_update(const S* src, S* dst, const Geo& g, 
   if constexpr (RECORD) {
     gamma_out[nb.ox[1] + nb.oy[1] + nb.oz[1]] = (float)gamma;
     if (guarded) atomicAdd(&ctr->guarded, 1ull);
+  }
+}
+
+// Two nodes of one row per thread, (xa, xb) = (x, x + 32) so every load and store instruction
+// of a warp stays coalesced; the collision runs once on float2 lanes with packed FP32x2
+// instructions. When xb is outside the box (vb false) lane 1 recomputes node xa and is not
+// stored. FP32 arithmetic only (S = float or uint16_t).
+template <typename S, int MODE, bool RECORD>
+__device__ __forceinline__ void node_update2(const S* src, S* dst, const Geo& g, uint32_t xa,
+                                             uint32_t xb, bool vb, uint32_t y, uint32_t z,
+                                             const CollideParams& cp, float* gamma_out,
+                                             StepCounters* ctr) {
+  using C = Codec<S>;
+  using Pat = Pattern<MODE>;
+  static_assert(std::is_same<typename C::R, float>::value, "FP32 arithmetic only");
+  Nbr na, nb;
+  na.init(g, xa, y, z);
+  nb.init(g, vb ? xb : xa, y, z);
+  float2 d[27];
+  Unroll<0, 27>::run([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    const S* base = src + (uint64_t)Pat::load_plane(I) * g.P;
+    const S* pa = base + na.template at<I, Pat::load_shift>();
+    const S* pb = base + nb.template at<I, Pat::load_shift>();
+    if constexpr (MODE == MODE_PULL) {
+      d[I].x = C::template load_ro<I>(pa);
+      d[I].y = C::template load_ro<I>(pb);
+    } else {
+      d[I].x = C::template load<I>(pa);
+      d[I].y = C::template load<I>(pb);
+    }
+  });
+  int guarded;
+  const float2 gamma = collide<float2>(d, cp, &guarded);
+  Unroll<0, 27>::run([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    S* base = dst + (uint64_t)Pat::store_plane(I) * g.P;
+    C::template store<I>(base + na.template at<I, Pat::store_shift>(), d[I].x);
+    if (vb) C::template store<I>(base + nb.template at<I, Pat::store_shift>(), d[I].y);
+  });
+  if constexpr (RECORD) {
+    gamma_out[na.ox[1] + na.oy[1] + na.oz[1]] = gamma.x;
+    if (vb) gamma_out[nb.ox[1] + nb.oy[1] + nb.oz[1]] = gamma.y;
+    const int n = __popc(guarded & (vb ? 3 : 1));
+    if (n) atomicAdd(&ctr->guarded, (unsigned long long)n);
   }
 }
 

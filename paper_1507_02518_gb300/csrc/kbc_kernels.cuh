@@ -27,6 +27,20 @@ __global__ void __launch_bounds__(MaxThreads<S>::value) step_kernel(const S* src
   node_update<S, MODE, RECORD>(src, dst, g, x, y, z, cp, gamma_out, ctr);
 }
 
+// Two nodes per thread with packed FP32x2 arithmetic: a block of 128 threads covers 256
+// consecutive x nodes of one row, each warp 64 of them as (x, x + 32) pairs.
+template <typename S, int MODE, bool RECORD>
+__global__ void __launch_bounds__(128, 3) pair_step_kernel(const S* src, S* dst, Geo g,
+                                                        CollideParams cp, float* gamma_out,
+                                                        StepCounters* ctr) {
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t xa = blockIdx.x * 256 + warp * 64 + lane;
+  const uint32_t xb = xa + 32;
+  if (xa >= g.nx) return;
+  node_update2<S, MODE, RECORD>(src, dst, g, xa, xb, xb < g.nx, blockIdx.y, blockIdx.z, cp,
+                                gamma_out, ctr);
+}
+
 // Batched ensemble: a persistent grid walks the work list; item k covers rows
 // [row0, row0 + nrows) (row = y + ny z) of one box.
 template <typename S, int MODE, bool RECORD>
@@ -341,9 +355,16 @@ static cudaError_t launch_step(const BoxView& b, const S* src, S* dst, const Geo
                                cudaStream_t st) {
   if (o.kernel == KERNEL_STAGED)
     return launch_staged<S, MODE, RECORD>(src, dst, g, cp, b.gamma, ctr, o.budget, o.stall, st);
-  if (o.kernel == KERNEL_PERSISTENT || o.kernel == KERNEL_AUTO)
+  if (o.kernel == KERNEL_PERSISTENT)
     return launch_persistent<S, MODE, RECORD>(src, dst, g, cp, b.gamma, ctr,
                                               (uint32_t)o.prefetch, st);
+  if constexpr (!std::is_same<S, double>::value) {
+    if (o.kernel == KERNEL_PACKED || o.kernel == KERNEL_AUTO) {
+      const dim3 grid((b.nx + 255) / 256, b.ny, b.nz);
+      pair_step_kernel<S, MODE, RECORD><<<grid, 128, 0, st>>>(src, dst, g, cp, b.gamma, ctr);
+      return cudaGetLastError();
+    }
+  }
   const dim3 block(o.bx, o.by, 1);
   const dim3 grid((b.nx + o.bx - 1) / o.bx, (b.ny + o.by - 1) / o.by, b.nz);
   step_kernel<S, MODE, RECORD><<<grid, block, 0, st>>>(src, dst, g, cp, b.gamma, ctr);

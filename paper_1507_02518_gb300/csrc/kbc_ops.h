@@ -25,7 +25,13 @@ struct StepCounters {
 };
 
 // kernel choice and test hooks of one step launch
-enum { KERNEL_AUTO = 0, KERNEL_DIRECT = 1, KERNEL_STAGED = 2, KERNEL_PERSISTENT = 3 };
+enum {
+  KERNEL_AUTO = 0,
+  KERNEL_DIRECT = 1,
+  KERNEL_STAGED = 2,
+  KERNEL_PERSISTENT = 3,
+  KERNEL_PACKED = 4
+};
 struct StepOpts {
   int bx, by;                 // block of the direct kernel
   int kernel;                 // KERNEL_*

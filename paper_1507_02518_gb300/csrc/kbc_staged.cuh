@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kSeg, StagedCfg<S>::min_blocks) staged_step_ke
         constexpr int I = decltype(ic)::value;
         d[I] = C::template load<I>(sb + I * L::ROW + H + tid + Pat::load_shift * cx(I));
       });
-      bool guarded;
+      int guarded;
       const R gamma = collide<R>(d, cp, &guarded);
       Nbr nb;
       nb.init(g, x0 + tid, y, z);

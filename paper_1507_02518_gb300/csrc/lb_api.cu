@@ -488,9 +488,12 @@ lb_status lb_set_time(lb_ctx* c, int64_t t) {
 
 lb_status lb_set_kernel(lb_ctx* c, int32_t kind) {
   if (!c) return LB_ERR_INVALID_ARG;
-  if (kind < LB_KERNEL_AUTO || kind > LB_KERNEL_PERSISTENT)
-    return fail(c, LB_ERR_INVALID_ARG, "kind must be LB_KERNEL_AUTO, _DIRECT, _STAGED or "
-                                       "_PERSISTENT");
+  if (kind < LB_KERNEL_AUTO || kind > LB_KERNEL_PACKED)
+    return fail(c, LB_ERR_INVALID_ARG, "kind must be LB_KERNEL_AUTO, _DIRECT, _STAGED, "
+                                       "_PERSISTENT or _PACKED");
+  if (kind == LB_KERNEL_PACKED && c->cfg.storage == LB_F64)
+    return fail(c, LB_ERR_UNSUPPORTED, "the packed FP32x2 kernel needs FP32 arithmetic "
+                                       "(LB_F32 or LB_F16 storage)");
   if (kind == LB_KERNEL_STAGED) {
     bool ok = false;
     dispatch(c, [&](auto ops) {

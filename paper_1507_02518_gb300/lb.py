@@ -22,9 +22,10 @@ LB_S_D, LB_S_DT, LB_S_DQ, LB_S_DTQ = range(4)
 LB_GAMMA_ESTIMATE, LB_GAMMA_LBGK, LB_GAMMA_RLB = range(3)
 LB_F64, LB_F32, LB_F16 = range(3)
 LB_PULL, LB_AA = range(2)
-LB_KERNEL_AUTO, LB_KERNEL_DIRECT, LB_KERNEL_STAGED, LB_KERNEL_PERSISTENT = range(4)
+LB_KERNEL_AUTO, LB_KERNEL_DIRECT, LB_KERNEL_STAGED, LB_KERNEL_PERSISTENT, \
+    LB_KERNEL_PACKED = range(5)
 KERNEL = {"auto": LB_KERNEL_AUTO, "direct": LB_KERNEL_DIRECT, "staged": LB_KERNEL_STAGED,
-          "persistent": LB_KERNEL_PERSISTENT}
+          "persistent": LB_KERNEL_PERSISTENT, "packed": LB_KERNEL_PACKED}
 
 STORAGE = {"f64": LB_F64, "f32": LB_F32, "f16": LB_F16}
 SCHEME = {"pull": LB_PULL, "aa": LB_AA}

@@ -165,13 +165,17 @@ def test_pull_and_aa_are_bitwise_identical(kbc, storage, steps):
 
 @pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
 @pytest.mark.parametrize("scheme", ["pull", "aa"])
-@pytest.mark.parametrize("shape", [(200, 3, 4), (256, 5, 3), (8, 6, 5)])
+@pytest.mark.parametrize("shape", [(200, 3, 4), (256, 5, 3), (8, 6, 5), (40, 3, 3)])
 def test_all_step_kernels_are_bitwise_identical(kbc, storage, scheme, shape):
     """Direct, shared-memory staged (bulk copies, several x-segments, ragged last segment,
-    periodic wrap inside the staged rows) and persistent (with and without L2 prefetch)."""
+    periodic wrap inside the staged rows), persistent (with and without L2 prefetch) and packed
+    FP32x2 (two nodes per thread, ragged pairs when nx is not a multiple of 64)."""
     f0 = seeded_state(*shape, seed=9)
     out = []
-    for kind, pf in (("direct", 2), ("staged", 2), ("persistent", 0), ("persistent", 3)):
+    kinds = [("direct", 2), ("staged", 2), ("persistent", 0), ("persistent", 3)]
+    if storage != "f64":
+        kinds.append(("packed", 0))
+    for kind, pf in kinds:
         lat = lattice(shape, storage=storage, scheme=scheme)
         lat.set_kernel(kind)
         lb.lb_set_prefetch(lat.ctx, pf)
@@ -185,11 +189,32 @@ def test_all_step_kernels_are_bitwise_identical(kbc, storage, scheme, shape):
     assert np.max(np.abs(out[0] - ref)) <= tol
 
 
-def test_staged_kernel_rejects_unaligned_rows(kbc):
+def test_kernel_choice_is_validated(kbc):
     lat = lattice((6, 4, 4), storage="f32")   # 24-byte rows
     with pytest.raises(lb.LBError) as e:
         lat.set_kernel("staged")
     assert e.value.status == lb.LB_ERR_UNSUPPORTED
+    lat64 = lattice((8, 4, 4), storage="f64")
+    with pytest.raises(lb.LBError) as e:
+        lat64.set_kernel("packed")
+    assert e.value.status == lb.LB_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("scheme", ["pull", "aa"])
+@pytest.mark.parametrize("shape", [(37, 5, 4), (3, 3, 3), (65, 4, 3)])
+def test_packed_kernel_on_ragged_rows(kbc, storage, scheme, shape):
+    """Packed pairs with an odd tail (x + 32 outside the row) equal the direct kernel."""
+    f0 = seeded_state(*shape, seed=4)
+    out = []
+    for kind in ("direct", "packed"):
+        lat = lattice(shape, storage=storage, scheme=scheme)
+        lat.set_kernel(kind)
+        lat.set_populations(f0)
+        lat.step(4)
+        out.append(lat.get_populations())
+        d = lat.diagnostics()
+    assert np.array_equal(out[0], out[1])
 
 
 def test_bounded_wait_reports_timeout_and_context_recovers(kbc):
