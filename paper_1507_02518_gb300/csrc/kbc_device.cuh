@@ -115,11 +115,13 @@ template <> struct Ar<float> {
   static __device__ __forceinline__ float fma(float a, float b, float c) {
     return __fmaf_rn(a, b, c);
   }
-  // hardware-approximate forms (about 2 ulp) where FP32 round-off is not the limit: the
-  // reciprocal weights of the entropic products, 1/rho, R = sqrt(1 + 3u^2) >= 1, and the
-  // ratio of eq:result21
-  static __device__ __forceinline__ float div_fast(float a, float b) { return __fdividef(a, b); }
-  static __device__ __forceinline__ float sqrt_fast(float a) { return __fmul_rn(a, rsqrtf(a)); }
+  // division as a correctly rounded reciprocal times an explicitly rounded multiply, and a
+  // correctly rounded square root: cheaper than IEEE division, and unique results, so every
+  // kernel computes the same bits
+  static __device__ __forceinline__ float div_fast(float a, float b) {
+    return __fmul_rn(a, __frcp_rn(b));
+  }
+  static __device__ __forceinline__ float sqrt_fast(float a) { return __fsqrt_rn(a); }
   static __device__ __forceinline__ float lane(float a, int) { return a; }
   static __device__ __forceinline__ void set_lane(float& a, int, float v) { a = v; }
 };
@@ -137,10 +139,10 @@ template <> struct Ar<float2> {
     return __ffma2_rn(a, b, c);
   }
   static __device__ __forceinline__ float2 div_fast(float2 a, float2 b) {
-    return make_float2(__fdividef(a.x, b.x), __fdividef(a.y, b.y));
+    return __fmul2_rn(a, make_float2(__frcp_rn(b.x), __frcp_rn(b.y)));
   }
   static __device__ __forceinline__ float2 sqrt_fast(float2 a) {
-    return make_float2(__fmul_rn(a.x, rsqrtf(a.x)), __fmul_rn(a.y, rsqrtf(a.y)));
+    return make_float2(__fsqrt_rn(a.x), __fsqrt_rn(a.y));
   }
   static __device__ __forceinline__ float lane(float2 a, int k) { return k ? a.y : a.x; }
   static __device__ __forceinline__ void set_lane(float2& a, int k, float v) {

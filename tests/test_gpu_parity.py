@@ -152,11 +152,15 @@ def test_fp64_launch_shapes_agree(kbc, bx, by):
 
 @pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
 @pytest.mark.parametrize("steps", [7, 8])
-def test_pull_and_aa_are_bitwise_identical(kbc, storage, steps):
+@pytest.mark.parametrize("kind", ["direct", "packed"])
+def test_pull_and_aa_are_bitwise_identical(kbc, storage, steps, kind):
+    if kind == "packed" and storage == "f64":
+        pytest.skip("no packed FP64")
     f0 = seeded_state(20, 12, 9)
     out = []
     for scheme in ("pull", "aa"):
         lat = lattice((20, 12, 9), storage=storage, scheme=scheme)
+        lat.set_kernel(kind)
         lat.set_populations(f0)
         lat.step(steps)
         out.append(lat.get_populations())
@@ -167,15 +171,13 @@ def test_pull_and_aa_are_bitwise_identical(kbc, storage, steps):
 @pytest.mark.parametrize("scheme", ["pull", "aa"])
 @pytest.mark.parametrize("shape", [(200, 3, 4), (256, 5, 3), (8, 6, 5), (40, 3, 3)])
 def test_all_step_kernels_are_bitwise_identical(kbc, storage, scheme, shape):
-    """Direct, shared-memory staged (bulk copies, several x-segments, ragged last segment,
-    periodic wrap inside the staged rows), persistent (with and without L2 prefetch) and packed
-    FP32x2 (two nodes per thread, ragged pairs when nx is not a multiple of 64)."""
+    """The scalar kernels -- direct, shared-memory staged (bulk copies, several x-segments,
+    ragged last segment, periodic wrap inside the staged rows), persistent (with and without L2
+    prefetch) -- give identical bits. The packed FP32x2 kernel rounds differently (same
+    operations, FP32x2 instruction stream) and is held to the oracle tolerance instead."""
     f0 = seeded_state(*shape, seed=9)
     out = []
-    kinds = [("direct", 2), ("staged", 2), ("persistent", 0), ("persistent", 3)]
-    if storage != "f64":
-        kinds.append(("packed", 0))
-    for kind, pf in kinds:
+    for kind, pf in (("direct", 2), ("staged", 2), ("persistent", 0), ("persistent", 3)):
         lat = lattice(shape, storage=storage, scheme=scheme)
         lat.set_kernel(kind)
         lb.lb_set_prefetch(lat.ctx, pf)
@@ -187,6 +189,14 @@ def test_all_step_kernels_are_bitwise_identical(kbc, storage, scheme, shape):
     ref, _, _ = oracle.run(f0, 5, oracle.beta(1e-3))
     tol = {"f64": FP64_TOL, "f32": 1e-6, "f16": 2e-3}[storage]
     assert np.max(np.abs(out[0] - ref)) <= tol
+    if storage != "f64":
+        lat = lattice(shape, storage=storage, scheme=scheme)
+        lat.set_kernel("packed")
+        lat.set_populations(f0)
+        lat.step(5)
+        packed = lat.get_populations()
+        assert np.max(np.abs(packed - ref)) <= tol
+        assert np.max(np.abs(packed - out[0])) <= tol
 
 
 def test_kernel_choice_is_validated(kbc):
@@ -204,17 +214,24 @@ def test_kernel_choice_is_validated(kbc):
 @pytest.mark.parametrize("scheme", ["pull", "aa"])
 @pytest.mark.parametrize("shape", [(37, 5, 4), (3, 3, 3), (65, 4, 3)])
 def test_packed_kernel_on_ragged_rows(kbc, storage, scheme, shape):
-    """Packed pairs with an odd tail (x + 32 outside the row) equal the direct kernel."""
+    """Packed pairs with an odd tail (x + 32 outside the row): every node written, each within
+    FP32 round-off of the oracle step taken from the same stored state."""
     f0 = seeded_state(*shape, seed=4)
-    out = []
-    for kind in ("direct", "packed"):
-        lat = lattice(shape, storage=storage, scheme=scheme)
-        lat.set_kernel(kind)
-        lat.set_populations(f0)
-        lat.step(4)
-        out.append(lat.get_populations())
-        d = lat.diagnostics()
-    assert np.array_equal(out[0], out[1])
+    lat = lattice(shape, storage=storage, scheme=scheme)
+    lat.set_kernel("packed")
+    lat.set_populations(f0)
+    lat.step(3)
+    got, ref, _ = one_step_reference(lat)
+    if storage == "f32":
+        assert np.max(np.abs(got - ref)) <= FP32_STEP_TOL
+    else:
+        h_got = ((got - W4) / W4).astype(np.float16).astype(np.float64)
+        h_ref = ((ref - W4) / W4).astype(np.float16)
+        ulp = np.spacing(np.abs(h_ref)).astype(np.float64)
+        diff = np.abs(h_got - h_ref.astype(np.float64)) * W4
+        assert np.all(diff <= ulp * W4 * 1.0001 + FP32_STEP_TOL)
+    d = lat.diagnostics()
+    assert d["nonfinite_count"] == 0
 
 
 def test_bounded_wait_reports_timeout_and_context_recovers(kbc):
@@ -268,7 +285,7 @@ def test_checkpoint_resume_is_bitwise(kbc, scheme, tmp_path):
 
 # ------------------------------------------------------------------ FP32 / FP16 parity
 
-def one_step_reference(lat, steps_before=0):
+def one_step_reference(lat):
     """Oracle step from exactly the state the GPU holds (decoded from its storage)."""
     f_in = lat.get_populations()
     ref, _, _ = oracle.run(f_in, 1, lat.beta)
@@ -277,11 +294,13 @@ def one_step_reference(lat, steps_before=0):
 
 
 @pytest.mark.parametrize("scheme", ["pull", "aa"])
-def test_fp32_one_step_parity(kbc, scheme):
+@pytest.mark.parametrize("kind", ["direct", "packed"])
+def test_fp32_one_step_parity(kbc, scheme, kind):
     n = 24
     rho, u = workloads.random_spectrum(n, 4, 0.04, seed=1)
     f0 = oracle.init_equilibrium(rho, u) * (1 + 1e-4 * workloads.population_noise(n, n, n, 5))
     lat = lattice((n, n, n), nu=2e-4, storage="f32", scheme=scheme)
+    lat.set_kernel(kind)
     lat.set_populations(f0)
     lat.step(3)                      # odd number: AA is in its swapped layout
     got, ref, _ = one_step_reference(lat)
@@ -290,11 +309,13 @@ def test_fp32_one_step_parity(kbc, scheme):
 
 
 @pytest.mark.parametrize("scheme", ["pull", "aa"])
-def test_fp16_one_step_parity_within_one_half_ulp(kbc, scheme):
+@pytest.mark.parametrize("kind", ["direct", "packed"])
+def test_fp16_one_step_parity_within_one_half_ulp(kbc, scheme, kind):
     n = 24
     rho, u = workloads.random_spectrum(n, 4, 0.04, seed=2)
     f0 = oracle.init_equilibrium(rho, u) * (1 + 1e-4 * workloads.population_noise(n, n, n, 6))
     lat = lattice((n, n, n), nu=2e-4, storage="f16", scheme=scheme)
+    lat.set_kernel(kind)
     lat.set_populations(f0)
     lat.step(2)
     got, ref, _ = one_step_reference(lat)
@@ -402,6 +423,7 @@ def test_batch_matches_single_boxes_bitwise(kbc, storage, scheme):
     for k, b in enumerate(boxes):
         nx, ny, nz = b["n"], b.get("ny", b["n"]), b.get("nz", b["n"])
         single = lb.Lattice(nx, ny, nz, nu=b["nu"], storage=storage, scheme=scheme)
+        single.set_kernel("direct")          # the batch kernel is scalar
         single.set_populations(states[k])
         single.step(7)
         got = np.empty((27, nz, ny, nx))
@@ -423,6 +445,7 @@ def test_batch_autotune_and_graph_replay(kbc):
     for _ in range(3):
         batch.step(4)            # the same graph replays
     ref = lb.Lattice(16, nu=1e-3, storage="f32", scheme="pull")
+    ref.set_kernel("direct")
     ref.init_field(rho, u)
     ref.step(12)
     got = np.empty((27, 16, 16, 16))
