@@ -49,8 +49,9 @@ VARIANTS = [
     {"name": "batch96_f32_pull", "field": "batch", "nbox": 96, "storage": "f32",
      "scheme": "pull", "steps": 200},
 ]
-# DRAM bytes per lattice update of the FP32 pull step kernel from an ncu capture, keyed by a
-# hash of the kernel sources; a changed kernel gets no traffic figure until re-profiled.
+# DRAM bytes per lattice update of the default FP32 pull step kernel (packed FP32x2) from an ncu
+# capture, keyed by a hash of the kernel sources; a changed kernel gets no traffic figure until
+# it is profiled again.
 NCU_TRAFFIC_PER_LUP = {}
 
 
@@ -391,8 +392,9 @@ def main_ours(args, rank, world, local):
         traffic = None
     rl = roofline(w["storage"], kernel_mlups, peak, peak_kind,
                   None if traffic is None else traffic * res["P"])
-    rl["kernel"] = "kbc::step_kernel<%s, %s>" % (
-        {"f64": "double", "f32": "float", "f16": "half"}[w["storage"]],
+    rl["kernel"] = "kbc::%s<%s, %s>" % (
+        "step_kernel" if w["storage"] == "f64" else "pair_step_kernel",
+        {"f64": "double", "f32": "float", "f16": "uint16 (half bits)"}[w["storage"]],
         "MODE_PULL" if w["scheme"] == "pull" else "MODE_AA_EVEN/ODD")
     rl["kernel_ms"] = round(kernel_ms, 5)
     del res["lat"]
