@@ -82,6 +82,35 @@ template <> struct Codec<uint16_t> {
   }
 };
 
+// Two values of one plane (nodes xa and xb) at a time, for the packed kernel.
+template <typename S> struct Codec2;
+template <> struct Codec2<float> {
+  template <int I, bool RO>
+  __device__ static __forceinline__ float2 load(const float* pa, const float* pb) {
+    return RO ? make_float2(__ldg(pa), __ldg(pb)) : make_float2(*pa, *pb);
+  }
+  template <int I> __device__ static __forceinline__ void store(float* pa, float* pb, bool vb,
+                                                              float2 v) {
+    *pa = v.x;
+    if (vb) *pb = v.y;
+  }
+};
+template <> struct Codec2<uint16_t> {
+  template <int I, bool RO>
+  __device__ static __forceinline__ float2 load(const uint16_t* pa, const uint16_t* pb) {
+    const uint16_t a = RO ? __ldg(pa) : *pa, b = RO ? __ldg(pb) : *pb;
+    const float2 h = __half22float2(__halves2half2(__ushort_as_half(a), __ushort_as_half(b)));
+    return __fmul2_rn(make_float2((float)wgt(I), (float)wgt(I)), h);
+  }
+  template <int I> __device__ static __forceinline__ void store(uint16_t* pa, uint16_t* pb,
+                                                              bool vb, float2 v) {
+    const float iw = (float)inv_wgt(I);
+    const __half2 h = __float22half2_rn(__fmul2_rn(make_float2(iw, iw), v));
+    *pa = __half_as_ushort(__low2half(h));
+    if (vb) *pb = __half_as_ushort(__high2half(h));
+  }
+};
+
 // guard on <dh|dh> (the paper is silent when it vanishes; gamma falls back to 2, LBGK)
 template <typename R> struct Guard;
 template <> struct Guard<double> { static constexpr double den = 1e-300; };
@@ -93,10 +122,16 @@ struct CollideParams {
   double beta;      // relaxation parameter of eq:Egeneral
   double two_beta;  // 2 beta
   double inv_beta;  // 1 / beta
+  float betaf, two_betaf, inv_betaf;  // the same, rounded once on the host for FP32 kernels
   int with_t;       // shear part includes t (Table 1)
   int with_q;       // shear part includes q (Table 1)
   int gamma_mode;   // GAMMA_*
 };
+
+// the parameter in the arithmetic precision (no FP64 conversion inside FP32 kernels)
+template <typename T> __device__ __forceinline__ T prec(double d, float f);
+template <> __device__ __forceinline__ double prec<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float prec<float>(double, float f) { return f; }
 
 // Explicitly rounded arithmetic. Every operation of the collision goes through these, so the
 // compiler does not contract them: the scalar kernels that inline collide<float|double>()
@@ -122,6 +157,7 @@ template <> struct Ar<float> {
   using Scalar = float;
   static constexpr int lanes = 1;
   static __device__ __forceinline__ float c(double v) { return (float)v; }
+  static __device__ __forceinline__ float bc(float v) { return v; }
   static __device__ __forceinline__ float neg(float a) { return -a; }
   static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
   static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
@@ -145,6 +181,7 @@ template <> struct Ar<float2> {
   using Scalar = float;
   static constexpr int lanes = 2;
   static __device__ __forceinline__ float2 c(double v) { return make_float2((float)v, (float)v); }
+  static __device__ __forceinline__ float2 bc(float v) { return make_float2(v, v); }
   static __device__ __forceinline__ float2 neg(float2 a) { return make_float2(-a.x, -a.y); }
   static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
   static __device__ __forceinline__ float2 sub(float2 a, float2 b) {
@@ -169,6 +206,7 @@ template <> struct Ar<double> {
   using Scalar = double;
   static constexpr int lanes = 1;
   static __device__ __forceinline__ double c(double v) { return v; }
+  static __device__ __forceinline__ double bc(double v) { return v; }
   static __device__ __forceinline__ double neg(double a) { return -a; }
   static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
   static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
@@ -325,7 +363,7 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, int* g
 
   // ---- dh, the two entropic products, and the part of the relaxation known before gamma
   // (listing steps 5-6): d <- d - 2 beta ds, dh kept for the gamma-dependent part
-  const R nb2 = O::c(-cp.two_beta);
+  const R nb2 = O::bc(-prec<T>(cp.two_beta, cp.two_betaf));
   R dh[27];
   R num = O::c(0.0), den = O::c(0.0);
   // (1 + gx)(1 + fy) - 1 for the 9 (a, b) pairs, shared by the three z levels
@@ -362,7 +400,7 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, int* g
   }
 
   // ---- stabilizer (eq:result21) and the rest of the relaxation (listing step 7)
-  const T ib = (T)cp.inv_beta;
+  const T ib = prec<T>(cp.inv_beta, cp.inv_betaf);
   R gamma = O::c(0.0);
   int gmask = 0;
 #pragma unroll
@@ -384,7 +422,7 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, int* g
     O::set_lane(gamma, k, gk);
   }
   *guarded = gmask;
-  const R nbg = O::neg(O::mul(O::c(cp.beta), gamma));
+  const R nbg = O::neg(O::mul(O::bc(prec<T>(cp.beta, cp.betaf)), gamma));
 #pragma unroll
   for (int i = 0; i < 27; ++i) d[i] = O::fma(nbg, dh[i], d[i]);
   return gamma;
@@ -529,23 +567,16 @@ __device__ __forceinline__ void node_update2(const S* src, S* dst, const Geo& g,
   Unroll<0, 27>::run([&](auto ic) {
     constexpr int I = decltype(ic)::value;
     const S* base = src + (uint64_t)Pat::load_plane(I) * g.P;
-    const S* pa = base + na.template at<I, Pat::load_shift>();
-    const S* pb = base + nb.template at<I, Pat::load_shift>();
-    if constexpr (MODE == MODE_PULL) {
-      d[I].x = C::template load_ro<I>(pa);
-      d[I].y = C::template load_ro<I>(pb);
-    } else {
-      d[I].x = C::template load<I>(pa);
-      d[I].y = C::template load<I>(pb);
-    }
+    d[I] = Codec2<S>::template load<I, MODE == MODE_PULL>(
+        base + na.template at<I, Pat::load_shift>(), base + nb.template at<I, Pat::load_shift>());
   });
   int guarded;
   const float2 gamma = collide<float2>(d, cp, &guarded);
   Unroll<0, 27>::run([&](auto ic) {
     constexpr int I = decltype(ic)::value;
     S* base = dst + (uint64_t)Pat::store_plane(I) * g.P;
-    C::template store<I>(base + na.template at<I, Pat::store_shift>(), d[I].x);
-    if (vb) C::template store<I>(base + nb.template at<I, Pat::store_shift>(), d[I].y);
+    Codec2<S>::template store<I>(base + na.template at<I, Pat::store_shift>(),
+                                 base + nb.template at<I, Pat::store_shift>(), vb, d[I]);
   });
   if constexpr (RECORD) {
     gamma_out[na.ox[1] + na.oy[1] + na.oz[1]] = gamma.x;

@@ -29,16 +29,42 @@ __global__ void __launch_bounds__(MaxThreads<S>::value) step_kernel(const S* src
 
 // Two nodes per thread with packed FP32x2 arithmetic: a block of 128 threads covers 256
 // consecutive x nodes of one row, each warp 64 of them as (x, x + 32) pairs.
+// The grid is persistent: SMs x resident blocks walk the items (256-node row segments).
 template <typename S, int MODE, bool RECORD>
 __global__ void __launch_bounds__(128, 3) pair_step_kernel(const S* src, S* dst, Geo g,
                                                         CollideParams cp, float* gamma_out,
-                                                        StepCounters* ctr) {
+                                                        StepCounters* ctr, uint32_t nseg,
+                                                        uint32_t nitems) {
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t xa = blockIdx.x * 256 + warp * 64 + lane;
-  const uint32_t xb = xa + 32;
-  if (xa >= g.nx) return;
-  node_update2<S, MODE, RECORD>(src, dst, g, xa, xb, xb < g.nx, blockIdx.y, blockIdx.z, cp,
-                                gamma_out, ctr);
+  for (uint32_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const uint32_t seg = item % nseg, row = item / nseg;
+    const uint32_t y = row % g.ny, z = row / g.ny;
+    const uint32_t xa = seg * 256 + warp * 64 + lane;
+    const uint32_t xb = xa + 32;
+    if (xa < g.nx)
+      node_update2<S, MODE, RECORD>(src, dst, g, xa, xb, xb < g.nx, y, z, cp, gamma_out, ctr);
+  }
+}
+
+template <typename S, int MODE, bool RECORD>
+static cudaError_t launch_pair(const S* src, S* dst, const Geo& g, const CollideParams& cp,
+                               float* gamma_out, StepCounters* ctr, cudaStream_t st) {
+  static int blocks_per_sm = 0, sms = 0;
+  auto kern = pair_step_kernel<S, MODE, RECORD>;
+  if (blocks_per_sm == 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, 128, 0);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+  }
+  const uint32_t nseg = (g.nx + 255) / 256;
+  const uint32_t nitems = nseg * g.ny * g.nz;
+  const uint32_t cap = (uint32_t)(sms * blocks_per_sm);
+  kern<<<nitems < cap ? nitems : cap, 128, 0, st>>>(src, dst, g, cp, gamma_out, ctr, nseg,
+                                                     nitems);
+  return cudaGetLastError();
 }
 
 // Batched ensemble: a persistent grid walks the work list; item k covers rows
@@ -61,6 +87,9 @@ __global__ void __launch_bounds__(MaxThreads<S>::value) batch_kernel(const BoxDe
     cp.beta = bd.beta;
     cp.two_beta = bd.two_beta;
     cp.inv_beta = bd.inv_beta;
+    cp.betaf = (float)bd.beta;
+    cp.two_betaf = (float)bd.two_beta;
+    cp.inv_betaf = (float)bd.inv_beta;
     cp.with_t = with_t;
     cp.with_q = with_q;
     cp.gamma_mode = gamma_mode;
@@ -335,6 +364,9 @@ inline CollideParams make_cp(double beta, int with_t, int with_q, int gamma_mode
   cp.beta = beta;
   cp.two_beta = 2.0 * beta;
   cp.inv_beta = 1.0 / beta;
+  cp.betaf = (float)cp.beta;
+  cp.two_betaf = (float)cp.two_beta;
+  cp.inv_betaf = (float)cp.inv_beta;
   cp.with_t = with_t;
   cp.with_q = with_q;
   cp.gamma_mode = gamma_mode;
@@ -359,11 +391,8 @@ static cudaError_t launch_step(const BoxView& b, const S* src, S* dst, const Geo
     return launch_persistent<S, MODE, RECORD>(src, dst, g, cp, b.gamma, ctr,
                                               (uint32_t)o.prefetch, st);
   if constexpr (!std::is_same<S, double>::value) {
-    if (o.kernel == KERNEL_PACKED || o.kernel == KERNEL_AUTO) {
-      const dim3 grid((b.nx + 255) / 256, b.ny, b.nz);
-      pair_step_kernel<S, MODE, RECORD><<<grid, 128, 0, st>>>(src, dst, g, cp, b.gamma, ctr);
-      return cudaGetLastError();
-    }
+    if (o.kernel == KERNEL_PACKED || o.kernel == KERNEL_AUTO)
+      return launch_pair<S, MODE, RECORD>(src, dst, g, cp, b.gamma, ctr, st);
   }
   const dim3 block(o.bx, o.by, 1);
   const dim3 grid((b.nx + o.bx - 1) / o.bx, (b.ny + o.by - 1) / o.by, b.nz);
