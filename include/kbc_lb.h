@@ -194,7 +194,12 @@ lb_ctx *lb_batch_box(lb_batch *b, int32_t box);
 lb_status lb_batch_step(lb_batch *b, int64_t n);
 /* Diagnostics of every box into out[nbox]. Synchronises. */
 lb_status lb_batch_diagnostics(lb_batch *b, lb_diag *out);
-/* Launch shape of the batched step: `threads` per block (multiple of 32, <= 512) and `tile`,
+/* Kernel of the batched step: LB_KERNEL_PACKED (two nodes per thread on FP32x2 instructions,
+ * 128 threads per block; LB_F32 / LB_F16), LB_KERNEL_DIRECT (one node per thread), or
+ * LB_KERNEL_AUTO (default: packed when the arithmetic is FP32). */
+lb_status lb_batch_set_kernel(lb_batch *b, int32_t kind);
+/* Launch shape of the batched step: `threads` per block (multiple of 32, <= 512; 128 for the
+ * packed kernel) and `tile`,
  * the target number of nodes per work item (an item is ceil(tile / nx) whole x-rows of one
  * box). The grid is persistent: SMs x resident blocks, clamped to the number of items. */
 lb_status lb_batch_set_tile(lb_batch *b, int32_t threads, int32_t tile);

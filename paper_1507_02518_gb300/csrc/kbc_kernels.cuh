@@ -29,41 +29,24 @@ __global__ void __launch_bounds__(MaxThreads<S>::value) step_kernel(const S* src
 
 // Two nodes per thread with packed FP32x2 arithmetic: a block of 128 threads covers 256
 // consecutive x nodes of one row, each warp 64 of them as (x, x + 32) pairs.
-// The grid is persistent: SMs x resident blocks walk the items (256-node row segments).
 template <typename S, int MODE, bool RECORD>
 __global__ void __launch_bounds__(128, 3) pair_step_kernel(const S* src, S* dst, Geo g,
                                                         CollideParams cp, float* gamma_out,
-                                                        StepCounters* ctr, uint32_t nseg,
-                                                        uint32_t nitems) {
+                                                        StepCounters* ctr) {
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (uint32_t item = blockIdx.x; item < nitems; item += gridDim.x) {
-    const uint32_t seg = item % nseg, row = item / nseg;
-    const uint32_t y = row % g.ny, z = row / g.ny;
-    const uint32_t xa = seg * 256 + warp * 64 + lane;
-    const uint32_t xb = xa + 32;
-    if (xa < g.nx)
-      node_update2<S, MODE, RECORD>(src, dst, g, xa, xb, xb < g.nx, y, z, cp, gamma_out, ctr);
-  }
+  const uint32_t xa = blockIdx.x * 256 + warp * 64 + lane;
+  const uint32_t xb = xa + 32;
+  if (xa >= g.nx) return;
+  node_update2<S, MODE, RECORD>(src, dst, g, xa, xb, xb < g.nx, blockIdx.y, blockIdx.z, cp,
+                                gamma_out, ctr);
 }
 
+// one block per 256-node row segment (a persistent grid measured slower on GB300)
 template <typename S, int MODE, bool RECORD>
 static cudaError_t launch_pair(const S* src, S* dst, const Geo& g, const CollideParams& cp,
                                float* gamma_out, StepCounters* ctr, cudaStream_t st) {
-  static int blocks_per_sm = 0, sms = 0;
-  auto kern = pair_step_kernel<S, MODE, RECORD>;
-  if (blocks_per_sm == 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, 128, 0);
-    if (e != cudaSuccess) return e;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (blocks_per_sm < 1) blocks_per_sm = 1;
-  }
-  const uint32_t nseg = (g.nx + 255) / 256;
-  const uint32_t nitems = nseg * g.ny * g.nz;
-  const uint32_t cap = (uint32_t)(sms * blocks_per_sm);
-  kern<<<nitems < cap ? nitems : cap, 128, 0, st>>>(src, dst, g, cp, gamma_out, ctr, nseg,
-                                                     nitems);
+  const dim3 grid((g.nx + 255) / 256, g.ny, g.nz);
+  pair_step_kernel<S, MODE, RECORD><<<grid, 128, 0, st>>>(src, dst, g, cp, gamma_out, ctr);
   return cudaGetLastError();
 }
 
@@ -102,6 +85,49 @@ __global__ void __launch_bounds__(MaxThreads<S>::value) batch_kernel(const BoxDe
       const uint32_t z = row / bd.ny;
       const uint32_t y = row - z * bd.ny;
       node_update<S, MODE, RECORD>(src, dst, g, x, y, z, cp, bd.gamma, bd.ctr);
+    }
+  }
+}
+
+// The packed form of batch_kernel: 128 threads, each item's rows cut into 64-node chunks,
+// each thread two nodes (x, x + 32) of a chunk with the FP32x2 collision.
+template <typename S, int MODE, bool RECORD>
+__global__ void __launch_bounds__(128, 3) batch_pair_kernel(const BoxDesc* __restrict__ boxes,
+                                                           const WorkItem* __restrict__ items,
+                                                           int nitems, int parity, int with_t,
+                                                           int with_q, int gamma_mode) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const WorkItem w = items[it];
+    const BoxDesc bd = boxes[w.box];
+    Geo g;
+    g.nx = bd.nx;
+    g.ny = bd.ny;
+    g.nz = bd.nz;
+    g.nxy = bd.nxy;
+    g.P = (uint64_t)bd.nxy * bd.nz;
+    CollideParams cp;
+    cp.beta = bd.beta;
+    cp.two_beta = bd.two_beta;
+    cp.inv_beta = bd.inv_beta;
+    cp.betaf = (float)bd.beta;
+    cp.two_betaf = (float)bd.two_beta;
+    cp.inv_betaf = (float)bd.inv_beta;
+    cp.with_t = with_t;
+    cp.with_q = with_q;
+    cp.gamma_mode = gamma_mode;
+    const S* src = (const S*)bd.pop[MODE == MODE_PULL ? parity : 0];
+    S* dst = (S*)bd.pop[MODE == MODE_PULL ? (parity ^ 1) : 0];
+    const uint32_t nchunk = (bd.nx + 63) / 64;
+    const uint32_t units = (uint32_t)w.nrows * nchunk * 32;
+    for (uint32_t u = threadIdx.x; u < units; u += blockDim.x) {
+      const uint32_t slot = u & 31, q = u >> 5;
+      const uint32_t rr = q / nchunk, chunk = q - rr * nchunk;
+      const uint32_t row = (uint32_t)w.row0 + rr;
+      const uint32_t z = row / bd.ny, y = row - z * bd.ny;
+      const uint32_t xa = chunk * 64 + slot, xb = xa + 32;
+      if (xa < bd.nx)
+        node_update2<S, MODE, RECORD>(src, dst, g, xa, xb, xb < bd.nx, y, z, cp, bd.gamma,
+                                      bd.ctr);
     }
   }
 }
@@ -475,8 +501,19 @@ cudaError_t Ops<S>::diag(const BoxView& b, int64_t t, bool with_gamma, void* ufi
 
 template <typename S, int MODE>
 static void launch_batch(const BoxDesc* boxes, const WorkItem* items, int nitems, int parity,
-                         bool record, int with_t, int with_q, int gamma_mode, int threads,
-                         int grid, cudaStream_t st) {
+                         bool record, bool packed, int with_t, int with_q, int gamma_mode,
+                         int threads, int grid, cudaStream_t st) {
+  if constexpr (!std::is_same<S, double>::value) {
+    if (packed) {
+      if (record)
+        batch_pair_kernel<S, MODE, true><<<grid, 128, 0, st>>>(boxes, items, nitems, parity,
+                                                               with_t, with_q, gamma_mode);
+      else
+        batch_pair_kernel<S, MODE, false><<<grid, 128, 0, st>>>(boxes, items, nitems, parity,
+                                                                with_t, with_q, gamma_mode);
+      return;
+    }
+  }
   if (record)
     batch_kernel<S, MODE, true><<<grid, threads, 0, st>>>(boxes, items, nitems, parity, with_t,
                                                           with_q, gamma_mode);
@@ -487,25 +524,38 @@ static void launch_batch(const BoxDesc* boxes, const WorkItem* items, int nitems
 
 template <typename S>
 cudaError_t Ops<S>::batch_step(const BoxDesc* boxes, const WorkItem* items, int nitems,
-                               int64_t t, bool record, int scheme, int with_t, int with_q,
-                               int gamma_mode, int threads, int grid, cudaStream_t st) {
+                               int64_t t, bool record, bool packed, int scheme, int with_t,
+                               int with_q, int gamma_mode, int threads, int grid,
+                               cudaStream_t st) {
   const int parity = (int)(t & 1);
   if (scheme == 0)
-    launch_batch<S, MODE_PULL>(boxes, items, nitems, parity, record, with_t, with_q, gamma_mode,
-                               threads, grid, st);
+    launch_batch<S, MODE_PULL>(boxes, items, nitems, parity, record, packed, with_t, with_q,
+                               gamma_mode, threads, grid, st);
   else if (parity == 0)
-    launch_batch<S, MODE_AA_EVEN>(boxes, items, nitems, parity, record, with_t, with_q,
+    launch_batch<S, MODE_AA_EVEN>(boxes, items, nitems, parity, record, packed, with_t, with_q,
                                   gamma_mode, threads, grid, st);
   else
-    launch_batch<S, MODE_AA_ODD>(boxes, items, nitems, parity, record, with_t, with_q,
+    launch_batch<S, MODE_AA_ODD>(boxes, items, nitems, parity, record, packed, with_t, with_q,
                                  gamma_mode, threads, grid, st);
   return cudaGetLastError();
 }
 
 template <typename S>
-int Ops<S>::batch_occupancy(int threads, int scheme) {
+int Ops<S>::batch_occupancy(int threads, int scheme, bool packed) {
   int blocks = 0;
-  cudaError_t e;
+  cudaError_t e = cudaErrorInvalidValue;
+  if constexpr (!std::is_same<S, double>::value) {
+    if (packed) {
+      if (scheme == 0)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &blocks, batch_pair_kernel<S, MODE_PULL, false>, 128, 0);
+      else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &blocks, batch_pair_kernel<S, MODE_AA_ODD, false>, 128, 0);
+      if (e != cudaSuccess || blocks < 1) blocks = 1;
+      return blocks;
+    }
+  }
   if (scheme == 0)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, batch_kernel<S, MODE_PULL, false>,
                                                       threads, 0);

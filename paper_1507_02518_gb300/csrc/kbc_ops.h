@@ -79,11 +79,13 @@ template <typename S> struct Ops {
   static cudaError_t diag(const BoxView& b, int64_t t, bool with_gamma, void* ufield,
                           double* partials, int nblocks, double* sums, cudaStream_t st);
   // one time step of every box of a batch over a work list
+  // (packed: the FP32x2 two-nodes-per-thread form, 128 threads; FP32 arithmetic only)
   static cudaError_t batch_step(const BoxDesc* boxes, const WorkItem* items, int nitems,
-                                int64_t t, bool record, int scheme, int with_t, int with_q,
-                                int gamma_mode, int threads, int grid, cudaStream_t st);
+                                int64_t t, bool record, bool packed, int scheme, int with_t,
+                                int with_q, int gamma_mode, int threads, int grid,
+                                cudaStream_t st);
   // resident blocks per SM of the batch kernel at this block size
-  static int batch_occupancy(int threads, int scheme);
+  static int batch_occupancy(int threads, int scheme, bool packed);
 };
 
 constexpr int kDiagSums = 16;   // layout of the diagnostics sums, see kbc_kernels.cuh

@@ -551,6 +551,7 @@ struct lb_batch {
   int nitems = 0;
   int threads = 256;
   int tile = 512;  // target nodes per work item
+  bool packed = false;  // FP32x2 two-nodes-per-thread kernel (FP32 arithmetic only)
   int grid = 1;
   cudaStream_t stream = nullptr;
   cudaStream_t capture_stream = nullptr;
@@ -651,9 +652,15 @@ lb_status build_items(lb_batch* b) {
   if (e != cudaSuccess) return bfail(b, LB_ERR_CUDA, std::string("uploading work list: ") + cudaGetErrorString(e));
   int occ = 1;
   switch (b->base_cfg.storage) {
-    case LB_F64: occ = kbc::Ops<double>::batch_occupancy(b->threads, b->base_cfg.scheme); break;
-    case LB_F32: occ = kbc::Ops<float>::batch_occupancy(b->threads, b->base_cfg.scheme); break;
-    default: occ = kbc::Ops<uint16_t>::batch_occupancy(b->threads, b->base_cfg.scheme); break;
+    case LB_F64:
+      occ = kbc::Ops<double>::batch_occupancy(b->threads, b->base_cfg.scheme, false);
+      break;
+    case LB_F32:
+      occ = kbc::Ops<float>::batch_occupancy(b->threads, b->base_cfg.scheme, b->packed);
+      break;
+    default:
+      occ = kbc::Ops<uint16_t>::batch_occupancy(b->threads, b->base_cfg.scheme, b->packed);
+      break;
   }
   const int cap = num_sms() * occ;
   b->grid = b->nitems < cap ? b->nitems : cap;
@@ -667,15 +674,17 @@ cudaError_t enqueue_batch_step(lb_batch* b, int64_t t, bool record, cudaStream_t
   const int wq = (c.variant == LB_S_DQ || c.variant == LB_S_DTQ);
   switch (c.storage) {
     case LB_F64:
-      return kbc::Ops<double>::batch_step(b->d_boxes, b->d_items, b->nitems, t, record, c.scheme,
-                                          wt, wq, c.gamma_mode, b->threads, b->grid, st);
+      return kbc::Ops<double>::batch_step(b->d_boxes, b->d_items, b->nitems, t, record, false,
+                                          c.scheme, wt, wq, c.gamma_mode, b->threads, b->grid,
+                                          st);
     case LB_F32:
-      return kbc::Ops<float>::batch_step(b->d_boxes, b->d_items, b->nitems, t, record, c.scheme,
-                                         wt, wq, c.gamma_mode, b->threads, b->grid, st);
+      return kbc::Ops<float>::batch_step(b->d_boxes, b->d_items, b->nitems, t, record,
+                                         b->packed, c.scheme, wt, wq, c.gamma_mode, b->threads,
+                                         b->grid, st);
     default:
       return kbc::Ops<uint16_t>::batch_step(b->d_boxes, b->d_items, b->nitems, t, record,
-                                            c.scheme, wt, wq, c.gamma_mode, b->threads, b->grid,
-                                            st);
+                                            b->packed, c.scheme, wt, wq, c.gamma_mode,
+                                            b->threads, b->grid, st);
   }
 }
 
@@ -727,6 +736,8 @@ lb_status lb_batch_create(const lb_config* cfgs, int32_t nbox, void* dev_buf, si
   b->d_boxes = (kbc::BoxDesc*)(base + L.boxes);
   b->d_items = (kbc::WorkItem*)(base + L.items);
   b->max_items = L.max_items;
+  b->packed = cfgs[0].storage != LB_F64;
+  if (b->packed) b->threads = 128;
   cudaError_t e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     g_create_error = std::string("creating capture stream: ") + cudaGetErrorString(e);
@@ -862,9 +873,23 @@ lb_status lb_batch_diagnostics(lb_batch* b, lb_diag* out) {
   return worst;
 }
 
+lb_status lb_batch_set_kernel(lb_batch* b, int32_t kind) {
+  if (!b) return LB_ERR_INVALID_ARG;
+  if (kind != LB_KERNEL_AUTO && kind != LB_KERNEL_DIRECT && kind != LB_KERNEL_PACKED)
+    return bfail(b, LB_ERR_INVALID_ARG, "batch kernel must be LB_KERNEL_AUTO, _DIRECT or _PACKED");
+  const bool fp32 = b->base_cfg.storage != LB_F64;
+  if (kind == LB_KERNEL_PACKED && !fp32)
+    return bfail(b, LB_ERR_UNSUPPORTED, "the packed kernel needs FP32 arithmetic");
+  b->packed = fp32 && kind != LB_KERNEL_DIRECT;
+  b->threads = b->packed ? 128 : 256;
+  return build_items(b);
+}
+
 lb_status lb_batch_set_tile(lb_batch* b, int32_t threads, int32_t tile) {
   if (!b) return LB_ERR_INVALID_ARG;
   const int maxt = b->base_cfg.storage == LB_F64 ? 256 : 512;
+  if (b->packed && threads != 128)
+    return bfail(b, LB_ERR_INVALID_ARG, "the packed batch kernel runs 128 threads per block");
   if (threads < 32 || threads > maxt || threads % 32 != 0 || tile < 32)
     return bfail(b, LB_ERR_INVALID_ARG, "threads must be a multiple of 32 in [32, 512] (256 for "
                                         "FP64); tile >= 32");
@@ -888,7 +913,7 @@ lb_status lb_batch_autotune(lb_batch* b, int32_t trial_steps, int32_t* best_thre
   b->t = b->views[0]->t;
   lb_status st = LB_OK;
   for (int th : cand_threads) {
-    if (th > maxt) continue;
+    if (th > maxt || (b->packed && th != 128)) continue;
     for (int tl : cand_tile) {
       b->threads = th;
       b->tile = tl;

@@ -67,7 +67,7 @@ SYMBOLS = ["lb_required_bytes", "lb_create", "lb_destroy", "lb_last_error", "lb_
            "lb_set_kernel", "lb_set_prefetch", "lb_set_wait_budget",
            "lb_batch_required_bytes", "lb_batch_create", "lb_batch_destroy",
            "lb_batch_last_error", "lb_batch_box", "lb_batch_step", "lb_batch_diagnostics",
-           "lb_batch_autotune", "lb_batch_set_tile"]
+           "lb_batch_autotune", "lb_batch_set_tile", "lb_batch_set_kernel"]
 
 
 class LBError(RuntimeError):
@@ -141,6 +141,8 @@ def load(path: str = LIB_PATH):
                                         ctypes.POINTER(d)]
         L.lb_batch_set_tile.restype = i32
         L.lb_batch_set_tile.argtypes = [vp, i32, i32]
+        L.lb_batch_set_kernel.restype = i32
+        L.lb_batch_set_kernel.argtypes = [vp, i32]
         _lib = L
         return L
 
@@ -286,6 +288,11 @@ def lb_batch_autotune(b, trial_steps: int):
     _check(load().lb_batch_autotune(b, int(trial_steps), ctypes.byref(th), ctypes.byref(tl),
                                     ctypes.byref(ms)), b, batch=True)
     return th.value, tl.value, ms.value
+
+
+def lb_batch_set_kernel(b, kind):
+    _check(load().lb_batch_set_kernel(b, KERNEL[kind] if isinstance(kind, str) else int(kind)),
+           b, batch=True)
 
 
 def lb_batch_set_tile(b, threads: int, tile: int):
@@ -446,3 +453,6 @@ class Batch:
 
     def set_tile(self, threads, tile):
         lb_batch_set_tile(self.handle, threads, tile)
+
+    def set_kernel(self, kind):
+        lb_batch_set_kernel(self.handle, kind)

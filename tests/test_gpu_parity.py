@@ -403,12 +403,15 @@ def test_nonfinite_is_reported(kbc):
 
 # ------------------------------------------------------------------ batched ensemble
 
-@pytest.mark.parametrize("storage,scheme", [("f32", "pull"), ("f32", "aa"), ("f64", "pull"),
-                                            ("f16", "aa")])
-def test_batch_matches_single_boxes_bitwise(kbc, storage, scheme):
+@pytest.mark.parametrize("storage,scheme,kind", [("f32", "pull", "direct"), ("f32", "aa", "direct"),
+                                                 ("f64", "pull", "direct"), ("f16", "aa", "direct"),
+                                                 ("f32", "pull", "packed"), ("f32", "aa", "packed"),
+                                                 ("f16", "aa", "packed"), ("f16", "pull", "packed")])
+def test_batch_matches_single_boxes_bitwise(kbc, storage, scheme, kind):
     boxes = [{"n": 12, "nu": 1e-3}, {"n": 9, "ny": 14, "nz": 5, "nu": 3e-4},
              {"n": 33, "ny": 4, "nz": 6, "nu": 2e-5}]
     batch = lb.Batch(boxes, storage=storage, scheme=scheme)
+    batch.set_kernel(kind)
     states = []
     for k, b in enumerate(boxes):
         nx, ny, nz = b["n"], b.get("ny", b["n"]), b.get("nz", b["n"])
@@ -417,13 +420,13 @@ def test_batch_matches_single_boxes_bitwise(kbc, storage, scheme):
         view = batch.box(k)
         ff = np.ascontiguousarray(f0)
         lb.lb_set_populations(view, ff.ctypes.data, False)
-    batch.set_tile(128, 64)
+    batch.set_tile(128, 64 if kind == "direct" else 256)
     batch.step(5)
     batch.step(2)
     for k, b in enumerate(boxes):
         nx, ny, nz = b["n"], b.get("ny", b["n"]), b.get("nz", b["n"])
         single = lb.Lattice(nx, ny, nz, nu=b["nu"], storage=storage, scheme=scheme)
-        single.set_kernel("direct")          # the batch kernel is scalar
+        single.set_kernel(kind)              # same kernel family as the batch
         single.set_populations(states[k])
         single.step(7)
         got = np.empty((27, nz, ny, nx))
@@ -445,7 +448,7 @@ def test_batch_autotune_and_graph_replay(kbc):
     for _ in range(3):
         batch.step(4)            # the same graph replays
     ref = lb.Lattice(16, nu=1e-3, storage="f32", scheme="pull")
-    ref.set_kernel("direct")
+    ref.set_kernel("packed")
     ref.init_field(rho, u)
     ref.step(12)
     got = np.empty((27, 16, 16, 16))
