@@ -49,10 +49,19 @@ VARIANTS = [
     {"name": "batch96_f32_pull", "field": "batch", "nbox": 96, "storage": "f32",
      "scheme": "pull", "steps": 200},
 ]
+# FP64-pipe instructions per lattice update of step_kernel<double> (ncu: the FP64 pipe was
+# 87.6 % busy, 598 instructions per node; profiles/step_kernel_f64_pull_hit128.md) and the
+# GB300 FP64 pipe peak of 2 instructions per SM per cycle.
+FP64_INSTR_PER_LUP = 598.0
+FP64_PIPE_PER_SM_PER_CYCLE = 2.0
 # DRAM bytes per lattice update of the default FP32 pull step kernel (packed FP32x2) from an ncu
 # capture, keyed by a hash of the kernel sources; a changed kernel gets no traffic figure until
 # it is profiled again.
-NCU_TRAFFIC_PER_LUP = {}
+NCU_TRAFFIC_PER_LUP = {
+    # pair_step_kernel<float, MODE_PULL> on 128^3: 226.53 MB read + 178.58 MB written
+    # for 2,097,152 nodes (profiles/pair_step_kernel_f32_pull_hit128.md)
+    "d5665b707ce5683e": 405.11e6 / 2097152,
+}
 
 
 def parse_workload(name):
@@ -401,6 +410,8 @@ def main_ours(args, rank, world, local):
     torch.cuda.empty_cache()
 
     variants = {}
+    clk_mhz = clk.summary().get("sm_mhz")
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
     if not args.no_variants:
         for v in VARIANTS:
             try:
@@ -424,6 +435,12 @@ def main_ours(args, rank, world, local):
                         "MLUPS": round(mlups, 1), "kernel_MLUPS": round(kml, 1), "steps": vs,
                         "frac_hbm": roofline(v["storage"], kml, peak, peak_kind)["frac"],
                         "kinetic_energy": d["kinetic_energy"], "gamma_mean": d["gamma_mean"]}
+                    if v["storage"] == "f64":
+                        clk = clk_mhz or 2070.0
+                        pipe_peak = FP64_PIPE_PER_SM_PER_CYCLE * sms * clk * 1e6
+                        variants[v["name"]]["bound"] = "alu (FP64 pipe)"
+                        variants[v["name"]]["frac_fp64_pipe"] = round(
+                            kml * 1e6 * FP64_INSTR_PER_LUP / pipe_peak, 4)
                     del r["lat"]
                 torch.cuda.empty_cache()
             except Exception as e:  # report, do not hide
