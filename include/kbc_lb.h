@@ -173,6 +173,28 @@ lb_status lb_set_block(lb_ctx *ctx, int32_t bx, int32_t by);
  * runs out (use a small budget). */
 lb_status lb_set_wait_budget(lb_ctx *ctx, uint64_t cycles, int32_t stall_copies);
 
+/* Diagnostics of a canonical population field with no memory allocation of any kind.
+ * The paper has no counterpart: this entry point exists for callers that cannot allocate
+ * device memory when they need diagnostics -- code running while a stream is captured into
+ * a CUDA graph, plugins whose host framework owns all device memory, monitors that must not
+ * change a job's footprint. It computes the fields of lb_diag that depend on the populations
+ * alone (mass, momentum, kinetic_energy, enstrophy, dissipation, nonfinite_count, nodes);
+ * gamma_mean and gamma_std are NaN, den_guard_count is 0 and step is -1.
+ *   f       device pointer to FP64 canonical populations f[27][P] (the layout of
+ *           lb_get_populations), P = nx*ny*nz <= 65536 nodes; larger boxes return
+ *           LB_ERR_INVALID_ARG before any GPU work.
+ *   nu      the kinematic viscosity in the dissipation, > 0.
+ *   stream  cudaStream_t the work is enqueued on; the call synchronises it.
+ *   out     host struct, filled on LB_OK and LB_ERR_NONFINITE.
+ * The work space is one file-scope __device__ array (about 1.6 MB) that stays on every GPU that
+ * loaded the library until the process exits. The first call on a device looks up that
+ * array's address with the device current, so make it before any stream capture begins. All
+ * calls share the array: calls that overlap on the GPU race and must be serialised by the
+ * caller. Errors: LB_ERR_INVALID_ARG, LB_ERR_CUDA, LB_ERR_NONFINITE; lb_last_error(NULL)
+ * explains. */
+lb_status lb_diagnostics_noalloc(int32_t nx, int32_t ny, int32_t nz, double nu, const double *f,
+                                 void *stream, lb_diag *out);
+
 /* ---------------------------------------------------------------- batched ensemble
  * Many independent periodic boxes of uneven sizes and viscosities, stepped together: one
  * kernel launch per time step walks a work list of (box, row-tile) items, and n steps are

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkbc.so")
-SOURCES = ["lb_api.cu", "kbc_f64.cu", "kbc_f32.cu", "kbc_f16.cu"]
+SOURCES = ["lb_api.cu", "kbc_f64.cu", "kbc_f32.cu", "kbc_f16.cu", "lb_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -130,6 +130,8 @@ lb_status check_device(std::string* why) {
 
 }  // namespace
 
+void kbc_set_thread_error(const std::string& msg) { g_create_error = msg; }
+
 struct lb_ctx {
   lb_config cfg;
   kbc::BoxView box;

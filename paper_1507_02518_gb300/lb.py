@@ -67,7 +67,8 @@ SYMBOLS = ["lb_required_bytes", "lb_create", "lb_destroy", "lb_last_error", "lb_
            "lb_set_kernel", "lb_set_prefetch", "lb_set_wait_budget",
            "lb_batch_required_bytes", "lb_batch_create", "lb_batch_destroy",
            "lb_batch_last_error", "lb_batch_box", "lb_batch_step", "lb_batch_diagnostics",
-           "lb_batch_autotune", "lb_batch_set_tile", "lb_batch_set_kernel"]
+           "lb_batch_autotune", "lb_batch_set_tile", "lb_batch_set_kernel",
+           "lb_diagnostics_noalloc"]
 
 
 class LBError(RuntimeError):
@@ -143,6 +144,8 @@ def load(path: str = LIB_PATH):
         L.lb_batch_set_tile.argtypes = [vp, i32, i32]
         L.lb_batch_set_kernel.restype = i32
         L.lb_batch_set_kernel.argtypes = [vp, i32]
+        L.lb_diagnostics_noalloc.restype = i32
+        L.lb_diagnostics_noalloc.argtypes = [i32, i32, i32, d, vp, vp, ctypes.POINTER(lb_diag)]
         _lib = L
         return L
 
@@ -206,6 +209,21 @@ def lb_diagnostics(ctx, raise_nonfinite: bool = True) -> lb_diag:
     if s == LB_ERR_NONFINITE and not raise_nonfinite:
         return d
     _check(s, ctx)
+    return d
+
+
+def lb_diagnostics_noalloc(nx: int, ny: int, nz: int, nu: float, f_dev_ptr: int, stream: int = 0,
+                           raise_nonfinite: bool = True) -> lb_diag:
+    """Diagnostics of a canonical FP64 population field already on the device, computed with
+    the library's static work space (no allocation; at most 65,536 nodes)."""
+    d = lb_diag()
+    s = load().lb_diagnostics_noalloc(int(nx), int(ny), int(nz), float(nu),
+                                      ctypes.c_void_p(f_dev_ptr), ctypes.c_void_p(stream),
+                                      ctypes.byref(d))
+    if s == LB_ERR_NONFINITE and not raise_nonfinite:
+        return d
+    if s != LB_OK:
+        raise LBError(s, lb_last_error(None))
     return d
 
 
