@@ -1,0 +1,133 @@
+"""Error of reduced-precision storage against FP64 on the same workload.
+
+Runs one workload with FP64 storage (FP64 collision; parity-checked against the CPU oracle by
+the test suite) and with FP32 / FP16 storage (FP32 collision), records the diagnostics every
+``every`` steps and reports, per precision:
+
+  * the relative error of the energy-decay curve k(t) and of the dissipation rate eps(t),
+  * the error of the enstrophy and of <gamma>,
+  * the maximum population error max |f - f_FP64| at the end, over all nodes or over a
+    sub-lattice taking every ``stride``-th node in each direction (the 768^3 -> 256^3
+    comparison uses stride 3), and the same for the velocity field.
+
+Usage::
+
+    python -m paper_1507_02518_gb300.precision --n 256 --steps 2000 --every 50 \\
+        --field spectrum --out result.json
+
+Everything runs through the library's C ABI; torch provides device memory.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+
+from . import lb, workloads
+
+
+def _field(kind, n, seed, device):
+    import torch
+    if kind == "spectrum":
+        rho, u = workloads.random_spectrum(n, 4.0, 0.04, seed)
+    elif kind == "kida":
+        rho, u = workloads.kida(n, 0.05)
+    else:
+        raise ValueError(kind)
+    return torch.from_numpy(u).to(device)
+
+
+def run_one(n, storage, scheme, nu, u_dev, steps, every, stride):
+    import torch
+    lat = lb.Lattice(n, nu=nu, storage=storage, scheme=scheme)
+    lat.init_field(None, u_dev)
+    curve = [lat.diagnostics()]
+    t0 = time.perf_counter()
+    done = 0
+    while done < steps:
+        c = min(every, steps - done)
+        lat.step(c)
+        done += c
+        curve.append(lat.diagnostics(raise_nonfinite=False))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    # the end state, sub-sampled on the device before it comes to the host
+    P = lat.P
+    f = torch.empty((27, P), dtype=torch.float64, device="cuda")
+    lb.lb_get_populations(lat.ctx, f.data_ptr(), True)
+    f = f.view(27, n, n, n)[:, ::stride, ::stride, ::stride].contiguous().cpu().numpy()
+    lat.close()
+    del lat
+    torch.cuda.empty_cache()
+    return {"curve": curve, "f": f, "wall_s": wall}
+
+
+def velocity(f):
+    v = np.array([[(i % 3) - 1, (i // 3) % 3 - 1, i // 9 - 1] for i in range(27)], float)
+    rho = f.sum(axis=0)
+    return np.einsum("ia,i...->a...", v, f) / rho
+
+
+def compare(ref, other):
+    out = {}
+    for key in ("kinetic_energy", "dissipation", "enstrophy"):
+        r = np.array([d[key] for d in ref["curve"]])
+        o = np.array([d[key] for d in other["curve"]])
+        out[key + "_max_rel_err"] = float(np.max(np.abs(o - r) / np.maximum(np.abs(r), 1e-300)))
+    g_r = np.array([d["gamma_mean"] for d in ref["curve"][1:]])
+    g_o = np.array([d["gamma_mean"] for d in other["curve"][1:]])
+    out["gamma_mean_max_abs_err"] = float(np.max(np.abs(g_o - g_r)))
+    out["population_max_abs_err"] = float(np.max(np.abs(other["f"] - ref["f"])))
+    ur, uo = velocity(ref["f"]), velocity(other["f"])
+    out["velocity_max_abs_err"] = float(np.max(np.abs(uo - ur)))
+    out["velocity_rms_rel_err"] = float(np.sqrt(np.mean((uo - ur) ** 2) / np.mean(ur ** 2)))
+    out["nonfinite"] = int(max(d["nonfinite_count"] for d in other["curve"]))
+    return out
+
+
+def study(n=256, steps=2000, every=50, field="spectrum", nu=2e-4, stride=1, seed=1,
+          precisions=(("f32", "pull"), ("f32", "aa"), ("f16", "aa")), ref_scheme="aa"):
+    import torch
+    lb.load()
+    u = _field(field, n, seed, "cuda")
+    ref = run_one(n, "f64", ref_scheme, nu, u, steps, every, stride)
+    res = {"n": n, "steps": steps, "every": every, "field": field, "nu": nu, "stride": stride,
+           "reference": {"storage": "f64", "scheme": ref_scheme, "wall_s": ref["wall_s"],
+                         "k": [d["kinetic_energy"] for d in ref["curve"]],
+                         "eps": [d["dissipation"] for d in ref["curve"]]},
+           "results": {}}
+    for storage, scheme in precisions:
+        o = run_one(n, storage, scheme, nu, u, steps, every, stride)
+        r = compare(ref, o)
+        r["wall_s"] = o["wall_s"]
+        res["results"]["%s_%s" % (storage, scheme)] = r
+    del u
+    torch.cuda.empty_cache()
+    return res
+
+
+def main(argv=None):
+    p = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    p.add_argument("--n", type=int, default=256)
+    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--every", type=int, default=50)
+    p.add_argument("--field", choices=["spectrum", "kida"], default="spectrum")
+    p.add_argument("--nu", type=float, default=2e-4)
+    p.add_argument("--stride", type=int, default=1)
+    p.add_argument("--out", default=None)
+    a = p.parse_args(argv)
+    res = study(a.n, a.steps, a.every, a.field, a.nu, a.stride)
+    text = json.dumps(res, indent=1)
+    if a.out:
+        with open(a.out, "w") as fh:
+            fh.write(text)
+    summary = {k: {kk: (round(vv, 8) if isinstance(vv, float) else vv) for kk, vv in v.items()}
+               for k, v in res["results"].items()}
+    print(json.dumps({"n": a.n, "steps": a.steps, "field": a.field, "results": summary}))
+
+
+if __name__ == "__main__":
+    main()
