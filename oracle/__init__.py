@@ -31,6 +31,7 @@ _lock = threading.Lock()
 _lib = None
 
 S_D, S_DT, S_DQ, S_DTQ = 0, 1, 2, 3
+S_CD, S_CDT, S_CDQ, S_CDTQ = 4, 5, 6, 7      # the same groups in the central-moment basis
 GAMMA_ESTIMATE, GAMMA_LBGK, GAMMA_RLB, GAMMA_EXACT = 0, 1, 2, 3
 DEN_GUARD = 1e-300
 
@@ -65,6 +66,8 @@ def lib():
             L.orc_moments.argtypes = [vp, vp, vp]
             L.orc_table1.argtypes = [vp, d, vp, vp, vp, vp]
             L.orc_moment_rep.argtypes = [vp, d, vp]
+            L.orc_central_moments.argtypes = [vp, vp, vp, vp]
+            L.orc_central_parts.argtypes = [vp, d, vp, vp, vp, vp, vp, vp]
             L.orc_collide.restype = ctypes.c_int
             L.orc_collide.argtypes = [vp, d, ctypes.c_int, ctypes.c_int, vp, vp]
             L.orc_collide_mirror.argtypes = [vp, d, ctypes.c_int, d, vp]
@@ -143,6 +146,22 @@ def moment_rep(M, rho):
     f = np.zeros(27)
     lib().orc_moment_rep(_p(M), float(rho), _p(f))
     return f
+
+
+def central_moments(f):
+    """(rho, u[3], Mc[3,3,3]) with Mc[p,q,r] = sum f (vx-ux)^p (vy-uy)^q (vz-uz)^r / rho."""
+    f = _f64(f)
+    rho, u, Mc = np.zeros(1), np.zeros(3), np.zeros(27)
+    lib().orc_central_moments(_p(f), _p(rho), _p(u), _p(Mc))
+    return float(rho[0]), u, Mc.reshape(3, 3, 3)
+
+
+def central_parts(Mc, rho, u):
+    """(k~, d~, t~, q~, h~) of the central-moment representation (appendix)."""
+    Mc, u = _f64(Mc).reshape(27), _f64(u)
+    parts = [np.zeros(27) for _ in range(5)]
+    lib().orc_central_parts(_p(Mc), float(rho), _p(u), *[_p(x) for x in parts])
+    return tuple(parts)
 
 
 def collide(f, beta_, variant=S_DTQ, gamma_mode=GAMMA_ESTIMATE):

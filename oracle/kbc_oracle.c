@@ -13,6 +13,9 @@
  *   natural moments ..................... eq:natmoments (straight sums over 27 velocities)
  *   moment representation of f .......... eq:moment_rep (Q labels read by counting powers)
  *   k / d / t / q parts ................. Table 1 (tab:s_parts)
+ *   central moments and central parts ... Sec. "Moment System" and the appendix (eq:cm1-eq:cm23,
+ *                                           eq:cmf000-eq:cmfxyz), as tensor products of the
+ *                                           one-dimensional central inverse
  *   collision ........................... the 7-step collision listing of Sec. KBC:
  *                                           rho,u -> f_eq -> s, s_eq -> ds -> dh -> gamma
  *                                           (eq:result21) -> f' = f - beta(2 ds + gamma dh)
@@ -190,24 +193,107 @@ void orc_moment_rep(const double *M, double rho, double *f) {
 }
 #undef MM
 
+/* Central moments (Sec. "Moment System for D3Q27"):
+ * rho Mc_pqr = sum_i f_i (vix - ux)^p (viy - uy)^q (viz - uz)^r, stored at [p*9 + q*3 + r]. */
+void orc_central_moments(const double *f, double *rho, double *u, double *Mc) {
+  double r = 0.0, m[3] = {0.0, 0.0, 0.0};
+  for (int i = 0; i < 27; ++i) {
+    r += f[i];
+    for (int a = 0; a < 3; ++a) m[a] += vcomp(i, a) * f[i];
+  }
+  *rho = r;
+  for (int a = 0; a < 3; ++a) u[a] = m[a] / r;
+  for (int p = 0; p < 3; ++p)
+    for (int q = 0; q < 3; ++q)
+      for (int s = 0; s < 3; ++s) {
+        double acc = 0.0;
+        for (int i = 0; i < 27; ++i) {
+          double w = f[i];
+          for (int k = 0; k < p; ++k) w *= vcomp(i, 0) - u[0];
+          for (int k = 0; k < q; ++k) w *= vcomp(i, 1) - u[1];
+          for (int k = 0; k < s; ++k) w *= vcomp(i, 2) - u[2];
+          acc += w;
+        }
+        Mc[p * 9 + q * 3 + s] = acc / r;
+      }
+}
+
+/* One-dimensional central inverse: coefficient of the p-th central moment in the population of
+ * velocity v, i.e. the inverse of the 3x3 matrix ((v - u)^p). The populations of
+ * eq:cmf000-eq:cmfxyz are its tensor products: f_abc = rho sum_pqr c(a;p) c(b;q) c(c;r) Mc_pqr. */
+static double cinv(int v, int p, double u) {
+  if (v == 0) return p == 0 ? 1.0 - u * u : (p == 1 ? -2.0 * u : -1.0);
+  const double s = (double)v;
+  return p == 0 ? u * (u + s) / 2.0 : (p == 1 ? (s + 2.0 * u) / 2.0 : 0.5);
+}
+
+/* Central-basis groups of every population (Sec. KBC, appendix): k~ from Mc_000 (the first
+ * central moments vanish), d~ from the deviatoric stress (Pi~, N~), t~ from the trace T~,
+ * q~ from the third-order Q~, h~ the remaining higher moments. With
+ * Mc_200 = (T + 2Nxz - Nyz)/3, Mc_020 = (T - Nxz + 2Nyz)/3, Mc_002 = (T - Nxz - Nyz)/3. */
+void orc_central_parts(const double *Mc, double rho, const double *u, double *k, double *d,
+                       double *t, double *q, double *h) {
+#define MC(p, q, r) Mc[(p) * 9 + (q) * 3 + (r)]
+  const double T = MC(2, 0, 0) + MC(0, 2, 0) + MC(0, 0, 2);
+  const double Nxz = MC(2, 0, 0) - MC(0, 0, 2), Nyz = MC(0, 2, 0) - MC(0, 0, 2);
+  for (int i = 0; i < 27; ++i) {
+    const int a = vcomp(i, 0), b = vcomp(i, 1), c = vcomp(i, 2);
+    double C[27];
+    for (int p = 0; p < 3; ++p)
+      for (int qq = 0; qq < 3; ++qq)
+        for (int r = 0; r < 3; ++r)
+          C[p * 9 + qq * 3 + r] = cinv(a, p, u[0]) * cinv(b, qq, u[1]) * cinv(c, r, u[2]);
+    const double c200 = C[18], c020 = C[6], c002 = C[2];
+    k[i] = rho * (C[0] * MC(0, 0, 0) + C[9] * MC(1, 0, 0) + C[3] * MC(0, 1, 0) + C[1] * MC(0, 0, 1));
+    t[i] = rho * T * (c200 + c020 + c002) / 3.0;
+    d[i] = rho * (Nxz * (2.0 * c200 - c020 - c002) / 3.0 + Nyz * (-c200 + 2.0 * c020 - c002) / 3.0 +
+                  C[12] * MC(1, 1, 0) + C[10] * MC(1, 0, 1) + C[4] * MC(0, 1, 1));
+    q[i] = rho * (C[15] * MC(1, 2, 0) + C[11] * MC(1, 0, 2) + C[21] * MC(2, 1, 0) +
+                  C[5] * MC(0, 1, 2) + C[19] * MC(2, 0, 1) + C[7] * MC(0, 2, 1) +
+                  C[13] * MC(1, 1, 1));
+    double rest = 0.0;
+    const int hm[8] = {2 * 3 + 2, 2 * 9 + 2, 2 * 9 + 2 * 3, 1 * 9 + 2 * 3 + 2, 2 * 9 + 1 * 3 + 2,
+                       2 * 9 + 2 * 3 + 1, 1 * 9 + 1 * 3 + 2, 1 * 9 + 2 * 3 + 1};
+    for (int j = 0; j < 8; ++j) rest += C[hm[j]] * Mc[hm[j]];
+    rest += C[2 * 9 + 1 * 3 + 1] * MC(2, 1, 1) + C[26] * MC(2, 2, 2);
+    h[i] = rho * rest;
+  }
+#undef MC
+}
+
 static void shear_part(const double *d, const double *t, const double *q, int variant,
                        double *s) {
-  const int with_t = (variant == ORC_S_DT || variant == ORC_S_DTQ);
-  const int with_q = (variant == ORC_S_DQ || variant == ORC_S_DTQ);
+  const int v = variant & 3;
+  const int with_t = (v == ORC_S_DT || v == ORC_S_DTQ);
+  const int with_q = (v == ORC_S_DQ || v == ORC_S_DTQ);
   for (int i = 0; i < 27; ++i) s[i] = d[i] + (with_t ? t[i] : 0.0) + (with_q ? q[i] : 0.0);
+}
+
+/* k and the s groups of a population vector in the basis the variant names */
+static void groups(const double *f, int variant, double *rho, double *u, double *k, double *d,
+                   double *t, double *q) {
+  if (variant >= ORC_S_CD) {
+    double Mc[27], h[27];
+    orc_central_moments(f, rho, u, Mc);
+    orc_central_parts(Mc, *rho, u, k, d, t, q, h);
+  } else {
+    double M[27];
+    orc_moments(f, rho, M);
+    u[0] = M[9];
+    u[1] = M[3];
+    u[2] = M[1];
+    orc_table1(M, *rho, k, d, t, q);
+  }
 }
 
 /* collision listing, steps 1-5: f_eq, ds = s - s_eq, dh = f - f_eq - ds */
 void orc_deltas(const double *f, int variant, double *feq, double *ds, double *dh) {
-  double rho, M[27], rho_eq, Meq[27];
+  double rho, u[3], rho_eq, u_eq[3];
   double k[27], d[27], t[27], q[27], s[27];
   double keq[27], deq[27], teq[27], qeq[27], seq[27];
-  orc_moments(f, &rho, M);                           /* step 1: rho, u */
-  const double u[3] = {M[9], M[3], M[1]};
+  groups(f, variant, &rho, u, k, d, t, q);           /* step 1: rho, u; step 3: s */
   orc_equilibrium(rho, u, feq);                      /* step 2 */
-  orc_moments(feq, &rho_eq, Meq);                    /* moments of f_eq by direct summation */
-  orc_table1(M, rho, k, d, t, q);                    /* step 3: s and s_eq from Table 1 */
-  orc_table1(Meq, rho_eq, keq, deq, teq, qeq);
+  groups(feq, variant, &rho_eq, u_eq, keq, deq, teq, qeq);  /* s_eq from the moments of f_eq */
   shear_part(d, t, q, variant, s);
   shear_part(deq, teq, qeq, variant, seq);
   for (int i = 0; i < 27; ++i) {
@@ -250,14 +336,11 @@ int orc_collide(const double *f, double beta, int variant, int gamma_mode, doubl
 
 /* eq:Egeneral with the mirror state eq:ksh-mirror, built from explicit k, s, h parts */
 void orc_collide_mirror(const double *f, double beta, int variant, double gamma, double *fout) {
-  double rho, M[27], feq[27], rho_eq, Meq[27];
+  double rho, u[3], feq[27], rho_eq, u_eq[3];
   double k[27], d[27], t[27], q[27], s[27], keq[27], deq[27], teq[27], qeq[27], seq[27];
-  orc_moments(f, &rho, M);
-  const double u[3] = {M[9], M[3], M[1]};
+  groups(f, variant, &rho, u, k, d, t, q);
   orc_equilibrium(rho, u, feq);
-  orc_moments(feq, &rho_eq, Meq);
-  orc_table1(M, rho, k, d, t, q);
-  orc_table1(Meq, rho_eq, keq, deq, teq, qeq);
+  groups(feq, variant, &rho_eq, u_eq, keq, deq, teq, qeq);
   shear_part(d, t, q, variant, s);
   shear_part(deq, teq, qeq, variant, seq);
   for (int i = 0; i < 27; ++i) {

@@ -22,8 +22,12 @@
 extern "C" {
 #endif
 
-/* choice of the shear part s (Sec. KBC, Table 1) */
-enum { ORC_S_D = 0, ORC_S_DT = 1, ORC_S_DQ = 2, ORC_S_DTQ = 3 };
+/* choice of the shear part s (Sec. KBC): natural-moment groups of Table 1, or the same groups
+ * in the central-moment basis (appendix, eq:cmf000-eq:cmfxyz) */
+enum {
+  ORC_S_D = 0, ORC_S_DT = 1, ORC_S_DQ = 2, ORC_S_DTQ = 3,
+  ORC_S_CD = 4, ORC_S_CDT = 5, ORC_S_CDQ = 6, ORC_S_CDTQ = 7
+};
 /* how the stabilizer gamma is chosen */
 enum {
   ORC_GAMMA_ESTIMATE = 0, /* eq:result21 (the method) */
@@ -41,6 +45,9 @@ void   orc_equilibrium(double rho, const double *u /*3*/, double *feq /*27*/);
 void   orc_moments(const double *f /*27*/, double *rho, double *M /*27: M[p*9+q*3+r]*/);
 void   orc_table1(const double *M, double rho, double *k, double *d, double *t, double *q);
 void   orc_moment_rep(const double *M, double rho, double *f /*27*/);
+void   orc_central_moments(const double *f, double *rho, double *u /*3*/, double *Mc /*27*/);
+void   orc_central_parts(const double *Mc, double rho, const double *u, double *k, double *d,
+                         double *t, double *q, double *h);
 int    orc_collide(const double *f, double beta, int variant, int gamma_mode,
                    double *fout, double *gamma_out);
 void   orc_collide_mirror(const double *f, double beta, int variant, double gamma, double *fout);

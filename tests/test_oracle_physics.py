@@ -21,7 +21,9 @@ def shear_amplitude(f, ny):
                                           (oracle.S_D, oracle.GAMMA_ESTIMATE),
                                           (oracle.S_DT, oracle.GAMMA_ESTIMATE),
                                           (oracle.S_DQ, oracle.GAMMA_ESTIMATE),
-                                          (oracle.S_DTQ, oracle.GAMMA_LBGK)])
+                                          (oracle.S_DTQ, oracle.GAMMA_LBGK),
+                                          (oracle.S_CD, oracle.GAMMA_ESTIMATE),
+                                          (oracle.S_CDTQ, oracle.GAMMA_ESTIMATE)])
 def test_shear_wave_decays_at_lattice_viscosity(variant, mode):
     """u_x = U sin(k y) decays as exp(-nu k^2 t), nu = c_s^2 (1/(2 beta) - 1/2), for any gamma."""
     nx, ny, nz = 3, 32, 3
