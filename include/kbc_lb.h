@@ -48,8 +48,12 @@ enum {
   LB_ERR_UNSUPPORTED = 6   /* valid but not built (e.g. no sm_103a device) */
 };
 
-/* Shear part s (Sec. KBC, Table 1): s in {d, d+t, d+q, d+t+q}. */
-enum { LB_S_D = 0, LB_S_DT = 1, LB_S_DQ = 2, LB_S_DTQ = 3 };
+/* Shear part s (Sec. KBC): s in {d, d+t, d+q, d+t+q} built on the natural moments (Table 1),
+ * or the same groups d~, t~, q~ built on the central moments (appendix, eq:cmf000 ff.). */
+enum {
+  LB_S_D = 0, LB_S_DT = 1, LB_S_DQ = 2, LB_S_DTQ = 3,
+  LB_S_CD = 4, LB_S_CDT = 5, LB_S_CDQ = 6, LB_S_CDTQ = 7
+};
 /* Stabilizer: eq:result21 (the method), or the fixed special cases named in Sec. KBC:
  * gamma = 2 (LBGK) and gamma = 1/beta (regularized LB). */
 enum { LB_GAMMA_ESTIMATE = 0, LB_GAMMA_LBGK = 1, LB_GAMMA_RLB = 2 };
@@ -147,6 +151,7 @@ lb_status lb_set_time(lb_ctx *ctx, int64_t t);
  *   LB_KERNEL_STAGED      the same items with the 27 source rows staged in shared memory by
  *                         asynchronous bulk copies in an mbarrier pipeline; needs
  *                         nx * sizeof(stored value) % 16 == 0 (else LB_ERR_UNSUPPORTED).
+ *                         Staged and persistent run the natural-moment variants only.
  *   LB_KERNEL_DIRECT      one thread per node over a full grid (lb_set_block), any nx.
  *   LB_KERNEL_AUTO        (default) packed for FP32 arithmetic, direct for LB_F64. */
 enum {

@@ -224,7 +224,7 @@ template <> struct Ar<double> {
 // One KBC collision on the shifted populations d[i] = f_i - W_i, in place (collision
 // listing of Sec. KBC); R holds one node (float, double) or two (float2). Returns gamma;
 // bit k of *guarded is set when lane k's <dh|dh> fell under the guard.
-template <typename R>
+template <typename R, bool CENTRAL = false>
 __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, int* guarded) {
   using O = Ar<R>;
   using T = typename O::Scalar;
@@ -290,15 +290,21 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, int* g
   const R A020 = O::fma(nrc23, ey, O::add(D020, nd3));
   const R A002 = O::fma(nrc23, ez, O::add(D002, nd3));
   const R ANxz = O::sub(A200, A002), ANyz = O::sub(A020, A002);
-  const R AT = cp.with_t ? O::add(O::add(A200, A020), A002) : O::c(0.0);
+  const R ATfull = O::add(O::add(A200, A020), A002);
+  const R AT = cp.with_t ? ATfull : O::c(0.0);
   const R nD100 = O::neg(D100), nD010 = O::neg(D010), nD001 = O::neg(D001);
   const R APxy = O::fma(nD100, uy, D110), APxz = O::fma(nD100, uz, D101);
   const R APyz = O::fma(nD010, uz, D011);
   const R qs = O::c(cp.with_q ? 1.0 : 0.0);
-  const R AQxyy = O::mul(qs, O::fma(nD100, m2y, D120)), AQxzz = O::mul(qs, O::fma(nD100, m2z, D102));
-  const R AQxxy = O::mul(qs, O::fma(nD010, m2x, D210)), AQyzz = O::mul(qs, O::fma(nD010, m2z, D012));
-  const R AQxxz = O::mul(qs, O::fma(nD001, m2x, D201)), AQyyz = O::mul(qs, O::fma(nD001, m2y, D021));
-  const R AQxyz = O::mul(qs, O::fma(O::neg(O::mul(D100, uy)), uz, D111));
+  // third-order natural deviations rho (M - M_eq), before the variant mask
+  const R RQxyy = O::fma(nD100, m2y, D120), RQxzz = O::fma(nD100, m2z, D102);
+  const R RQxxy = O::fma(nD010, m2x, D210), RQyzz = O::fma(nD010, m2z, D012);
+  const R RQxxz = O::fma(nD001, m2x, D201), RQyyz = O::fma(nD001, m2y, D021);
+  const R RQxyz = O::fma(O::neg(O::mul(D100, uy)), uz, D111);
+  const R AQxyy = O::mul(qs, RQxyy), AQxzz = O::mul(qs, RQxzz);
+  const R AQxxy = O::mul(qs, RQxxy), AQyzz = O::mul(qs, RQyzz);
+  const R AQxxz = O::mul(qs, RQxxz), AQyyz = O::mul(qs, RQyyz);
+  const R AQxyz = O::mul(qs, RQxyz);
 
   // Table 1 per velocity class: ds = d + t + q evaluated on the deviations
   const R c16 = O::c(1.0 / 6.0), half = O::c(0.5), quarter = O::c(0.25);
@@ -372,19 +378,83 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, int* g
   for (int b = 0; b < 3; ++b)
 #pragma unroll
     for (int a = 0; a < 3; ++a) Pab[a + 3 * b] = O::fma(gx[a], fy[b], O::add(gx[a], fy[b]));
+  // Central-moment variants (appendix): the shear part is built on the central moments.
+  // Their deviations follow from the natural ones because rho and u are conserved: second
+  // order unchanged, third order rho dMc_120 = rho dM_120 - 2 uy rho dM_110 - ux rho dM_020
+  // and its permutations, rho dMc_111 = rho dM_111 - ux rho dM_011 - uy rho dM_101 - uz rho dM_110.
+  // ds_i = sum over the s moments of cx(a;p) cy(b;q) cz(c;r) rho dMc_pqr with the 1D central
+  // inverse c(0) = [1 - u^2, -2u, -1], c(+-1) = [u(u +- 1)/2, u +- 1/2, 1/2].
+  R B200, B020, B002, Bc[7], cxv[3][3], cyv[3][3], czv[3][3];
+  if constexpr (CENTRAL) {
+    const R tr = cp.with_t ? O::c(0.0) : O::mul(ATfull, O::c(1.0 / 3.0));
+    B200 = O::sub(A200, tr);
+    B020 = O::sub(A020, tr);
+    B002 = O::sub(A002, tr);
+    const R two = O::c(2.0);
+    Bc[0] = O::mul(qs, O::fma(O::neg(ux), A020, O::fma(O::neg(O::mul(two, uy)), APxy, RQxyy)));  // 120
+    Bc[1] = O::mul(qs, O::fma(O::neg(ux), A002, O::fma(O::neg(O::mul(two, uz)), APxz, RQxzz)));  // 102
+    Bc[2] = O::mul(qs, O::fma(O::neg(uy), A200, O::fma(O::neg(O::mul(two, ux)), APxy, RQxxy)));  // 210
+    Bc[3] = O::mul(qs, O::fma(O::neg(uy), A002, O::fma(O::neg(O::mul(two, uz)), APyz, RQyzz)));  // 012
+    Bc[4] = O::mul(qs, O::fma(O::neg(uz), A200, O::fma(O::neg(O::mul(two, ux)), APxz, RQxxz)));  // 201
+    Bc[5] = O::mul(qs, O::fma(O::neg(uz), A020, O::fma(O::neg(O::mul(two, uy)), APyz, RQyyz)));  // 021
+    Bc[6] = O::mul(qs, O::fma(O::neg(uz), APxy,
+                              O::fma(O::neg(uy), APxz, O::fma(O::neg(ux), APyz, RQxyz))));   // 111
+    auto coef = [&](R u, R (&cv)[3][3]) {  // cv[v+1][p]
+      const R hu = O::mul(O::c(0.5), u);
+      const R uu = O::mul(u, u);
+      cv[0][0] = O::sub(O::mul(hu, u), hu);          // u(u - 1)/2
+      cv[1][0] = O::sub(one, uu);                    // 1 - u^2
+      cv[2][0] = O::add(O::mul(hu, u), hu);          // u(u + 1)/2
+      cv[0][1] = O::sub(u, O::c(0.5));
+      cv[1][1] = O::mul(O::c(-2.0), u);
+      cv[2][1] = O::add(u, O::c(0.5));
+      cv[0][2] = O::c(0.5);
+      cv[1][2] = O::c(-1.0);
+      cv[2][2] = O::c(0.5);
+    };
+    coef(ux, cxv);
+    coef(uy, cyv);
+    coef(uz, czv);
+  }
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     R cn = O::c(0.0), cd = O::c(0.0);
+    // z stage of the central shear part: Zpq = sum_r cz(c;r) rho dMc_pqr
+    R Z00, Z01, Z02, Z10, Z11, Z12, Z20, Z21;
+    if constexpr (CENTRAL) {
+      const R* cz = czv[c];
+      Z20 = O::fma(cz[1], Bc[4], O::mul(cz[0], B200));
+      Z02 = O::fma(cz[1], Bc[5], O::mul(cz[0], B020));
+      Z00 = O::mul(cz[2], B002);
+      Z11 = O::fma(cz[1], Bc[6], O::mul(cz[0], APxy));
+      Z10 = O::fma(cz[2], Bc[1], O::mul(cz[1], APxz));
+      Z01 = O::fma(cz[2], Bc[3], O::mul(cz[1], APyz));
+      Z12 = O::mul(cz[0], Bc[0]);
+      Z21 = O::mul(cz[0], Bc[2]);
+    }
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
       R rn = O::c(0.0), rd = O::c(0.0);
+      R Y0, Y1, Y2;  // y stage: Yp = sum_q cy(b;q) Zpq
+      if constexpr (CENTRAL) {
+        const R* cy = cyv[b];
+        Y0 = O::fma(cy[2], Z02, O::fma(cy[1], Z01, O::mul(cy[0], Z00)));
+        Y1 = O::fma(cy[2], Z12, O::fma(cy[1], Z11, O::mul(cy[0], Z10)));
+        Y2 = O::fma(cy[1], Z21, O::mul(cy[0], Z20));
+      }
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const int i = a + 3 * b + 9 * c;
         // (f_eq_i - W_i)/W_i = (1 + gx)(1 + fy)(1 + fz) - 1 without cancellation
         const R P = Pab[a + 3 * b];
         const R G = O::fma(P, fz[c], O::add(P, fz[c]));
-        const R dsi = ds_of(a - 1, b - 1, c - 1);
+        R dsi;
+        if constexpr (CENTRAL) {
+          const R* cx = cxv[a];
+          dsi = O::fma(cx[2], Y2, O::fma(cx[1], Y1, O::mul(cx[0], Y0)));
+        } else {
+          dsi = ds_of(a - 1, b - 1, c - 1);
+        }
         const R dhi = O::sub(O::fma(O::c(-wgt(i)), G, d[i]), dsi);
         const R t1 = O::mul(rx[a], dhi);
         rn = O::fma(t1, dsi, rn);
@@ -516,7 +586,7 @@ template <int N> struct Unroll<N, N> {
 // ------------------------------------------------------------------ the fused node update
 // Loads f(x, t) of node (x, y, z) by the pattern of MODE, collides, stores f'(x) where
 // f(t+1) expects it. src and dst are the same buffer in the AA modes.
-template <typename S, int MODE, bool RECORD>
+template <typename S, int MODE, bool RECORD, bool CENTRAL = false>
 __device__ __forceinline__ void node_update(const S* src, S* dst, const Geo& g, uint32_t x,
                                             uint32_t y, uint32_t z, const CollideParams& cp,
                                             float* gamma_out, StepCounters* ctr) {
@@ -536,7 +606,7 @@ __device__ __forceinline__ void node_update(const S* src, S* dst, const Geo& g, 
     }
   });
   int guarded;
-  const R gamma = collide<R>(d, cp, &guarded);
+  const R gamma = collide<R, CENTRAL>(d, cp, &guarded);
   Unroll<0, 27>::run([&](auto ic) {
     constexpr int I = decltype(ic)::value;
     S* p = dst + (uint64_t)Pat::store_plane(I) * g.P + nb.template at<I, Pat::store_shift>();
@@ -552,7 +622,7 @@ __device__ __forceinline__ void node_update(const S* src, S* dst, const Geo& g, 
 // of a warp stays coalesced; the collision runs once on float2 lanes with packed FP32x2
 // instructions. When xb is outside the box (vb false) lane 1 recomputes node xa and is not
 // stored. FP32 arithmetic only (S = float or uint16_t).
-template <typename S, int MODE, bool RECORD>
+template <typename S, int MODE, bool RECORD, bool CENTRAL = false>
 __device__ __forceinline__ void node_update2(const S* src, S* dst, const Geo& g, uint32_t xa,
                                              uint32_t xb, bool vb, uint32_t y, uint32_t z,
                                              const CollideParams& cp, float* gamma_out,
@@ -571,7 +641,7 @@ __device__ __forceinline__ void node_update2(const S* src, S* dst, const Geo& g,
         base + na.template at<I, Pat::load_shift>(), base + nb.template at<I, Pat::load_shift>());
   });
   int guarded;
-  const float2 gamma = collide<float2>(d, cp, &guarded);
+  const float2 gamma = collide<float2, CENTRAL>(d, cp, &guarded);
   Unroll<0, 27>::run([&](auto ic) {
     constexpr int I = decltype(ic)::value;
     S* base = dst + (uint64_t)Pat::store_plane(I) * g.P;

@@ -17,19 +17,19 @@ namespace kbc {
 template <typename S> struct MaxThreads { static constexpr int value = 512; };
 template <> struct MaxThreads<double> { static constexpr int value = 256; };
 
-template <typename S, int MODE, bool RECORD>
+template <typename S, int MODE, bool RECORD, bool CENTRAL>
 __global__ void __launch_bounds__(MaxThreads<S>::value) step_kernel(const S* src, S* dst, Geo g, CollideParams cp,
                                                    float* gamma_out, StepCounters* ctr) {
   const uint32_t x = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t y = blockIdx.y * blockDim.y + threadIdx.y;
   const uint32_t z = blockIdx.z;
   if (x >= g.nx || y >= g.ny) return;
-  node_update<S, MODE, RECORD>(src, dst, g, x, y, z, cp, gamma_out, ctr);
+  node_update<S, MODE, RECORD, CENTRAL>(src, dst, g, x, y, z, cp, gamma_out, ctr);
 }
 
 // Two nodes per thread with packed FP32x2 arithmetic: a block of 128 threads covers 256
 // consecutive x nodes of one row, each warp 64 of them as (x, x + 32) pairs.
-template <typename S, int MODE, bool RECORD>
+template <typename S, int MODE, bool RECORD, bool CENTRAL>
 __global__ void __launch_bounds__(128, 3) pair_step_kernel(const S* src, S* dst, Geo g,
                                                         CollideParams cp, float* gamma_out,
                                                         StepCounters* ctr) {
@@ -37,22 +37,23 @@ __global__ void __launch_bounds__(128, 3) pair_step_kernel(const S* src, S* dst,
   const uint32_t xa = blockIdx.x * 256 + warp * 64 + lane;
   const uint32_t xb = xa + 32;
   if (xa >= g.nx) return;
-  node_update2<S, MODE, RECORD>(src, dst, g, xa, xb, xb < g.nx, blockIdx.y, blockIdx.z, cp,
-                                gamma_out, ctr);
+  node_update2<S, MODE, RECORD, CENTRAL>(src, dst, g, xa, xb, xb < g.nx, blockIdx.y, blockIdx.z,
+                                         cp, gamma_out, ctr);
 }
 
 // one block per 256-node row segment (a persistent grid measured slower on GB300)
-template <typename S, int MODE, bool RECORD>
+template <typename S, int MODE, bool RECORD, bool CENTRAL>
 static cudaError_t launch_pair(const S* src, S* dst, const Geo& g, const CollideParams& cp,
                                float* gamma_out, StepCounters* ctr, cudaStream_t st) {
   const dim3 grid((g.nx + 255) / 256, g.ny, g.nz);
-  pair_step_kernel<S, MODE, RECORD><<<grid, 128, 0, st>>>(src, dst, g, cp, gamma_out, ctr);
+  pair_step_kernel<S, MODE, RECORD, CENTRAL><<<grid, 128, 0, st>>>(src, dst, g, cp, gamma_out,
+                                                                   ctr);
   return cudaGetLastError();
 }
 
 // Batched ensemble: a persistent grid walks the work list; item k covers rows
 // [row0, row0 + nrows) (row = y + ny z) of one box.
-template <typename S, int MODE, bool RECORD>
+template <typename S, int MODE, bool RECORD, bool CENTRAL>
 __global__ void __launch_bounds__(MaxThreads<S>::value) batch_kernel(const BoxDesc* __restrict__ boxes,
                                                     const WorkItem* __restrict__ items,
                                                     int nitems, int parity, int with_t,
@@ -84,14 +85,14 @@ __global__ void __launch_bounds__(MaxThreads<S>::value) batch_kernel(const BoxDe
       const uint32_t x = k - (k / bd.nx) * bd.nx;
       const uint32_t z = row / bd.ny;
       const uint32_t y = row - z * bd.ny;
-      node_update<S, MODE, RECORD>(src, dst, g, x, y, z, cp, bd.gamma, bd.ctr);
+      node_update<S, MODE, RECORD, CENTRAL>(src, dst, g, x, y, z, cp, bd.gamma, bd.ctr);
     }
   }
 }
 
 // The packed form of batch_kernel: 128 threads, each item's rows cut into 64-node chunks,
 // each thread two nodes (x, x + 32) of a chunk with the FP32x2 collision.
-template <typename S, int MODE, bool RECORD>
+template <typename S, int MODE, bool RECORD, bool CENTRAL>
 __global__ void __launch_bounds__(128, 3) batch_pair_kernel(const BoxDesc* __restrict__ boxes,
                                                            const WorkItem* __restrict__ items,
                                                            int nitems, int parity, int with_t,
@@ -126,8 +127,8 @@ __global__ void __launch_bounds__(128, 3) batch_pair_kernel(const BoxDesc* __res
       const uint32_t z = row / bd.ny, y = row - z * bd.ny;
       const uint32_t xa = chunk * 64 + slot, xb = xa + 32;
       if (xa < bd.nx)
-        node_update2<S, MODE, RECORD>(src, dst, g, xa, xb, xb < bd.nx, y, z, cp, bd.gamma,
-                                      bd.ctr);
+        node_update2<S, MODE, RECORD, CENTRAL>(src, dst, g, xa, xb, xb < bd.nx, y, z, cp,
+                                               bd.gamma, bd.ctr);
     }
   }
 }
@@ -407,23 +408,34 @@ inline int grid_for(uint64_t cnt, int threads) {
   return (int)blocks;
 }
 
+template <typename S, int MODE, bool RECORD, bool CENTRAL>
+static cudaError_t launch_step_c(const BoxView& b, const S* src, S* dst, const Geo& g,
+                                 const CollideParams& cp, const StepOpts& o, StepCounters* ctr,
+                                 cudaStream_t st) {
+  if constexpr (!CENTRAL) {
+    if (o.kernel == KERNEL_STAGED)
+      return launch_staged<S, MODE, RECORD>(src, dst, g, cp, b.gamma, ctr, o.budget, o.stall, st);
+    if (o.kernel == KERNEL_PERSISTENT)
+      return launch_persistent<S, MODE, RECORD>(src, dst, g, cp, b.gamma, ctr,
+                                                (uint32_t)o.prefetch, st);
+  }
+  if constexpr (!std::is_same<S, double>::value) {
+    if (o.kernel == KERNEL_PACKED || o.kernel == KERNEL_AUTO)
+      return launch_pair<S, MODE, RECORD, CENTRAL>(src, dst, g, cp, b.gamma, ctr, st);
+  }
+  const dim3 block(o.bx, o.by, 1);
+  const dim3 grid((b.nx + o.bx - 1) / o.bx, (b.ny + o.by - 1) / o.by, b.nz);
+  step_kernel<S, MODE, RECORD, CENTRAL><<<grid, block, 0, st>>>(src, dst, g, cp, b.gamma, ctr);
+  return cudaGetLastError();
+}
+
 template <typename S, int MODE, bool RECORD>
 static cudaError_t launch_step(const BoxView& b, const S* src, S* dst, const Geo& g,
                                const CollideParams& cp, const StepOpts& o, StepCounters* ctr,
                                cudaStream_t st) {
-  if (o.kernel == KERNEL_STAGED)
-    return launch_staged<S, MODE, RECORD>(src, dst, g, cp, b.gamma, ctr, o.budget, o.stall, st);
-  if (o.kernel == KERNEL_PERSISTENT)
-    return launch_persistent<S, MODE, RECORD>(src, dst, g, cp, b.gamma, ctr,
-                                              (uint32_t)o.prefetch, st);
-  if constexpr (!std::is_same<S, double>::value) {
-    if (o.kernel == KERNEL_PACKED || o.kernel == KERNEL_AUTO)
-      return launch_pair<S, MODE, RECORD>(src, dst, g, cp, b.gamma, ctr, st);
-  }
-  const dim3 block(o.bx, o.by, 1);
-  const dim3 grid((b.nx + o.bx - 1) / o.bx, (b.ny + o.by - 1) / o.by, b.nz);
-  step_kernel<S, MODE, RECORD><<<grid, block, 0, st>>>(src, dst, g, cp, b.gamma, ctr);
-  return cudaGetLastError();
+  if (b.central)
+    return launch_step_c<S, MODE, RECORD, true>(b, src, dst, g, cp, o, ctr, st);
+  return launch_step_c<S, MODE, RECORD, false>(b, src, dst, g, cp, o, ctr, st);
 }
 
 template <typename S>
@@ -499,44 +511,56 @@ cudaError_t Ops<S>::diag(const BoxView& b, int64_t t, bool with_gamma, void* ufi
   return cudaGetLastError();
 }
 
-template <typename S, int MODE>
-static void launch_batch(const BoxDesc* boxes, const WorkItem* items, int nitems, int parity,
-                         bool record, bool packed, int with_t, int with_q, int gamma_mode,
-                         int threads, int grid, cudaStream_t st) {
+template <typename S, int MODE, bool CENTRAL>
+static void launch_batch_c(const BoxDesc* boxes, const WorkItem* items, int nitems, int parity,
+                           bool record, bool packed, int with_t, int with_q, int gamma_mode,
+                           int threads, int grid, cudaStream_t st) {
   if constexpr (!std::is_same<S, double>::value) {
     if (packed) {
       if (record)
-        batch_pair_kernel<S, MODE, true><<<grid, 128, 0, st>>>(boxes, items, nitems, parity,
-                                                               with_t, with_q, gamma_mode);
+        batch_pair_kernel<S, MODE, true, CENTRAL><<<grid, 128, 0, st>>>(
+            boxes, items, nitems, parity, with_t, with_q, gamma_mode);
       else
-        batch_pair_kernel<S, MODE, false><<<grid, 128, 0, st>>>(boxes, items, nitems, parity,
-                                                                with_t, with_q, gamma_mode);
+        batch_pair_kernel<S, MODE, false, CENTRAL><<<grid, 128, 0, st>>>(
+            boxes, items, nitems, parity, with_t, with_q, gamma_mode);
       return;
     }
   }
   if (record)
-    batch_kernel<S, MODE, true><<<grid, threads, 0, st>>>(boxes, items, nitems, parity, with_t,
-                                                          with_q, gamma_mode);
+    batch_kernel<S, MODE, true, CENTRAL><<<grid, threads, 0, st>>>(boxes, items, nitems, parity,
+                                                                   with_t, with_q, gamma_mode);
   else
-    batch_kernel<S, MODE, false><<<grid, threads, 0, st>>>(boxes, items, nitems, parity, with_t,
-                                                           with_q, gamma_mode);
+    batch_kernel<S, MODE, false, CENTRAL><<<grid, threads, 0, st>>>(boxes, items, nitems, parity,
+                                                                    with_t, with_q, gamma_mode);
+}
+
+template <typename S, int MODE>
+static void launch_batch(const BoxDesc* boxes, const WorkItem* items, int nitems, int parity,
+                         bool record, bool packed, bool central, int with_t, int with_q,
+                         int gamma_mode, int threads, int grid, cudaStream_t st) {
+  if (central)
+    launch_batch_c<S, MODE, true>(boxes, items, nitems, parity, record, packed, with_t, with_q,
+                                  gamma_mode, threads, grid, st);
+  else
+    launch_batch_c<S, MODE, false>(boxes, items, nitems, parity, record, packed, with_t, with_q,
+                                   gamma_mode, threads, grid, st);
 }
 
 template <typename S>
 cudaError_t Ops<S>::batch_step(const BoxDesc* boxes, const WorkItem* items, int nitems,
                                int64_t t, bool record, bool packed, int scheme, int with_t,
-                               int with_q, int gamma_mode, int threads, int grid,
+                               int with_q, int central, int gamma_mode, int threads, int grid,
                                cudaStream_t st) {
   const int parity = (int)(t & 1);
   if (scheme == 0)
-    launch_batch<S, MODE_PULL>(boxes, items, nitems, parity, record, packed, with_t, with_q,
-                               gamma_mode, threads, grid, st);
+    launch_batch<S, MODE_PULL>(boxes, items, nitems, parity, record, packed, central, with_t,
+                               with_q, gamma_mode, threads, grid, st);
   else if (parity == 0)
-    launch_batch<S, MODE_AA_EVEN>(boxes, items, nitems, parity, record, packed, with_t, with_q,
-                                  gamma_mode, threads, grid, st);
+    launch_batch<S, MODE_AA_EVEN>(boxes, items, nitems, parity, record, packed, central, with_t,
+                                  with_q, gamma_mode, threads, grid, st);
   else
-    launch_batch<S, MODE_AA_ODD>(boxes, items, nitems, parity, record, packed, with_t, with_q,
-                                 gamma_mode, threads, grid, st);
+    launch_batch<S, MODE_AA_ODD>(boxes, items, nitems, parity, record, packed, central, with_t,
+                                 with_q, gamma_mode, threads, grid, st);
   return cudaGetLastError();
 }
 
@@ -548,20 +572,20 @@ int Ops<S>::batch_occupancy(int threads, int scheme, bool packed) {
     if (packed) {
       if (scheme == 0)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &blocks, batch_pair_kernel<S, MODE_PULL, false>, 128, 0);
+            &blocks, batch_pair_kernel<S, MODE_PULL, false, false>, 128, 0);
       else
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &blocks, batch_pair_kernel<S, MODE_AA_ODD, false>, 128, 0);
+            &blocks, batch_pair_kernel<S, MODE_AA_ODD, false, false>, 128, 0);
       if (e != cudaSuccess || blocks < 1) blocks = 1;
       return blocks;
     }
   }
   if (scheme == 0)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, batch_kernel<S, MODE_PULL, false>,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, batch_kernel<S, MODE_PULL, false, false>,
                                                       threads, 0);
   else
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks,
-                                                      batch_kernel<S, MODE_AA_ODD, false>,
+                                                      batch_kernel<S, MODE_AA_ODD, false, false>,
                                                       threads, 0);
   if (e != cudaSuccess || blocks < 1) blocks = 1;
   return blocks;

@@ -13,6 +13,7 @@ struct BoxView {
   float* gamma;        // [P] stabilizer of the last recorded collision
   double beta;
   int with_t, with_q, gamma_mode;
+  int central;         // shear part in the central-moment basis
   int scheme;          // 0 pull, 1 AA
 };
 
@@ -82,7 +83,7 @@ template <typename S> struct Ops {
   // (packed: the FP32x2 two-nodes-per-thread form, 128 threads; FP32 arithmetic only)
   static cudaError_t batch_step(const BoxDesc* boxes, const WorkItem* items, int nitems,
                                 int64_t t, bool record, bool packed, int scheme, int with_t,
-                                int with_q, int gamma_mode, int threads, int grid,
+                                int with_q, int central, int gamma_mode, int threads, int grid,
                                 cudaStream_t st);
   // resident blocks per SM of the batch kernel at this block size
   static int batch_occupancy(int threads, int scheme, bool packed);

@@ -47,8 +47,8 @@ bool valid_config(const lb_config* c, std::string* why) {
     *why = "nu must be finite and > 0";
     return false;
   }
-  if (c->variant < LB_S_D || c->variant > LB_S_DTQ) {
-    *why = "variant must be LB_S_D..LB_S_DTQ";
+  if (c->variant < LB_S_D || c->variant > LB_S_CDTQ) {
+    *why = "variant must be LB_S_D..LB_S_DTQ or LB_S_CD..LB_S_CDTQ";
     return false;
   }
   if (c->gamma_mode < LB_GAMMA_ESTIMATE || c->gamma_mode > LB_GAMMA_RLB) {
@@ -182,8 +182,10 @@ void setup_ctx(lb_ctx* c, const lb_config* cfg, char* base, const BoxLayout& B,
   c->box.pop[1] = base + B.pop1;
   c->box.gamma = (float*)(base + B.gamma);
   c->box.beta = 1.0 / (6.0 * cfg->nu + 1.0);  // eq:viscosity with c_s^2 = 1/3
-  c->box.with_t = (cfg->variant == LB_S_DT || cfg->variant == LB_S_DTQ);
-  c->box.with_q = (cfg->variant == LB_S_DQ || cfg->variant == LB_S_DTQ);
+  const int v = cfg->variant & 3;  // the central variants repeat the natural groups
+  c->box.with_t = (v == LB_S_DT || v == LB_S_DTQ);
+  c->box.with_q = (v == LB_S_DQ || v == LB_S_DTQ);
+  c->box.central = cfg->variant >= LB_S_CD;
   c->box.gamma_mode = cfg->gamma_mode;
   c->box.scheme = cfg->scheme;
   c->counters = (kbc::StepCounters*)(base + B.counters);
@@ -493,6 +495,9 @@ lb_status lb_set_kernel(lb_ctx* c, int32_t kind) {
   if (kind < LB_KERNEL_AUTO || kind > LB_KERNEL_PACKED)
     return fail(c, LB_ERR_INVALID_ARG, "kind must be LB_KERNEL_AUTO, _DIRECT, _STAGED, "
                                        "_PERSISTENT or _PACKED");
+  if ((kind == LB_KERNEL_STAGED || kind == LB_KERNEL_PERSISTENT) && c->box.central)
+    return fail(c, LB_ERR_UNSUPPORTED, "the staged and persistent kernels implement the natural-"
+                                       "moment variants only");
   if (kind == LB_KERNEL_PACKED && c->cfg.storage == LB_F64)
     return fail(c, LB_ERR_UNSUPPORTED, "the packed FP32x2 kernel needs FP32 arithmetic "
                                        "(LB_F32 or LB_F16 storage)");
@@ -672,20 +677,22 @@ lb_status build_items(lb_batch* b) {
 
 cudaError_t enqueue_batch_step(lb_batch* b, int64_t t, bool record, cudaStream_t st) {
   const lb_config& c = b->base_cfg;
-  const int wt = (c.variant == LB_S_DT || c.variant == LB_S_DTQ);
-  const int wq = (c.variant == LB_S_DQ || c.variant == LB_S_DTQ);
+  const int v = c.variant & 3;
+  const int wt = (v == LB_S_DT || v == LB_S_DTQ);
+  const int wq = (v == LB_S_DQ || v == LB_S_DTQ);
+  const int central = c.variant >= LB_S_CD;
   switch (c.storage) {
     case LB_F64:
       return kbc::Ops<double>::batch_step(b->d_boxes, b->d_items, b->nitems, t, record, false,
-                                          c.scheme, wt, wq, c.gamma_mode, b->threads, b->grid,
-                                          st);
+                                          c.scheme, wt, wq, central, c.gamma_mode, b->threads,
+                                          b->grid, st);
     case LB_F32:
       return kbc::Ops<float>::batch_step(b->d_boxes, b->d_items, b->nitems, t, record,
-                                         b->packed, c.scheme, wt, wq, c.gamma_mode, b->threads,
-                                         b->grid, st);
+                                         b->packed, c.scheme, wt, wq, central, c.gamma_mode,
+                                         b->threads, b->grid, st);
     default:
       return kbc::Ops<uint16_t>::batch_step(b->d_boxes, b->d_items, b->nitems, t, record,
-                                            b->packed, c.scheme, wt, wq, c.gamma_mode,
+                                            b->packed, c.scheme, wt, wq, central, c.gamma_mode,
                                             b->threads, b->grid, st);
   }
 }

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libkbc.so")
 
 LB_OK, LB_ERR_INVALID_ARG, LB_ERR_OOM, LB_ERR_CUDA, LB_ERR_NONFINITE, LB_ERR_TIMEOUT, \
     LB_ERR_UNSUPPORTED = range(7)
-LB_S_D, LB_S_DT, LB_S_DQ, LB_S_DTQ = range(4)
+LB_S_D, LB_S_DT, LB_S_DQ, LB_S_DTQ, LB_S_CD, LB_S_CDT, LB_S_CDQ, LB_S_CDTQ = range(8)
 LB_GAMMA_ESTIMATE, LB_GAMMA_LBGK, LB_GAMMA_RLB = range(3)
 LB_F64, LB_F32, LB_F16 = range(3)
 LB_PULL, LB_AA = range(2)
@@ -29,7 +29,8 @@ KERNEL = {"auto": LB_KERNEL_AUTO, "direct": LB_KERNEL_DIRECT, "staged": LB_KERNE
 
 STORAGE = {"f64": LB_F64, "f32": LB_F32, "f16": LB_F16}
 SCHEME = {"pull": LB_PULL, "aa": LB_AA}
-VARIANT = {"d": LB_S_D, "d+t": LB_S_DT, "d+q": LB_S_DQ, "d+t+q": LB_S_DTQ}
+VARIANT = {"d": LB_S_D, "d+t": LB_S_DT, "d+q": LB_S_DQ, "d+t+q": LB_S_DTQ,
+           "cd": LB_S_CD, "cd+ct": LB_S_CDT, "cd+cq": LB_S_CDQ, "cd+ct+cq": LB_S_CDTQ}
 GAMMA = {"estimate": LB_GAMMA_ESTIMATE, "lbgk": LB_GAMMA_LBGK, "rlb": LB_GAMMA_RLB}
 BYTES_PER_VALUE = {LB_F64: 8, LB_F32: 4, LB_F16: 2}
 

@@ -53,7 +53,7 @@ def test_required_bytes_and_validation(lib):
                 lb.make_config(1 << 11, 1 << 10, 1 << 10)):
         assert lb.lb_required_bytes(bad) == 0
     c_bad = lb.make_config(32)
-    c_bad.variant = 9
+    c_bad.variant = 8
     assert lb.lb_required_bytes(c_bad) == 0
 
 

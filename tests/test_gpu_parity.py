@@ -123,7 +123,7 @@ def test_fp64_matches_oracle_ragged_boxes(kbc, shape, scheme):
     assert np.max(np.abs(lat.get_populations() - ref)) <= FP64_TOL
 
 
-@pytest.mark.parametrize("variant", ["d", "d+t", "d+q", "d+t+q"])
+@pytest.mark.parametrize("variant", ["d", "d+t", "d+q", "d+t+q", "cd", "cd+ct", "cd+cq", "cd+ct+cq"])
 @pytest.mark.parametrize("gamma", ["estimate", "lbgk", "rlb"])
 def test_fp64_matches_oracle_variants(kbc, variant, gamma):
     f0 = seeded_state(10, 9, 8, noise=1e-3)
@@ -199,6 +199,45 @@ def test_all_step_kernels_are_bitwise_identical(kbc, storage, scheme, shape):
         assert np.max(np.abs(packed - out[0])) <= tol
 
 
+@pytest.mark.parametrize("variant", ["cd", "cd+ct+cq"])
+@pytest.mark.parametrize("scheme", ["pull", "aa"])
+@pytest.mark.parametrize("kind", ["direct", "packed"])
+def test_central_variants_fp32_one_step_parity(kbc, variant, scheme, kind):
+    n = 24
+    rho, u = workloads.random_spectrum(n, 4, 0.04, seed=8)
+    f0 = oracle.init_equilibrium(rho, u) * (1 + 1e-4 * workloads.population_noise(n, n, n, 9))
+    lat = lattice((n, n, n), nu=2e-4, storage="f32", scheme=scheme, variant=variant)
+    lat.set_kernel(kind)
+    lat.set_populations(f0)
+    lat.step(3)
+    f_in = lat.get_populations()
+    ref, _, _ = oracle.run(f_in, 1, lat.beta, lb.VARIANT[variant])
+    lat.step(1)
+    assert np.max(np.abs(lat.get_populations() - ref)) <= FP32_STEP_TOL
+
+
+def test_central_batch_matches_single_box(kbc):
+    boxes = [{"n": 12, "nu": 1e-3}, {"n": 9, "ny": 14, "nz": 5, "nu": 3e-4}]
+    batch = lb.Batch(boxes, storage="f32", scheme="aa", variant="cd+ct+cq")
+    states = []
+    for k, b in enumerate(boxes):
+        nx, ny, nz = b["n"], b.get("ny", b["n"]), b.get("nz", b["n"])
+        f0 = np.ascontiguousarray(seeded_state(nx, ny, nz, seed=40 + k))
+        states.append(f0)
+        lb.lb_set_populations(batch.box(k), f0.ctypes.data, False)
+    batch.step(5)
+    for k, b in enumerate(boxes):
+        nx, ny, nz = b["n"], b.get("ny", b["n"]), b.get("nz", b["n"])
+        single = lb.Lattice(nx, ny, nz, nu=b["nu"], storage="f32", scheme="aa",
+                            variant="cd+ct+cq")
+        single.set_kernel("packed")
+        single.set_populations(states[k])
+        single.step(5)
+        got = np.empty((27, nz, ny, nx))
+        lb.lb_get_populations(batch.box(k), got.ctypes.data, False)
+        assert np.array_equal(got, single.get_populations())
+
+
 def test_kernel_choice_is_validated(kbc):
     lat = lattice((6, 4, 4), storage="f32")   # 24-byte rows
     with pytest.raises(lb.LBError) as e:
@@ -207,6 +246,10 @@ def test_kernel_choice_is_validated(kbc):
     lat64 = lattice((8, 4, 4), storage="f64")
     with pytest.raises(lb.LBError) as e:
         lat64.set_kernel("packed")
+    assert e.value.status == lb.LB_ERR_UNSUPPORTED
+    latc = lattice((8, 4, 4), storage="f32", variant="cd")
+    with pytest.raises(lb.LBError) as e:
+        latc.set_kernel("staged")
     assert e.value.status == lb.LB_ERR_UNSUPPORTED
 
 
