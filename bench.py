@@ -48,6 +48,9 @@ VARIANTS = [
      "storage": "f16", "scheme": "aa", "diag_every": 50, "steps": 200},
     {"name": "batch96_f32_pull", "field": "batch", "nbox": 96, "storage": "f32",
      "scheme": "pull", "steps": 200},
+    {"name": "hit256_f32_pull_central", "n": 256, "field": "spectrum", "k0": 4.0, "urms": 0.04,
+     "nu": 2e-4, "seed": 1, "storage": "f32", "scheme": "pull", "diag_every": 50, "steps": 400,
+     "variant": "cd+ct+cq"},
 ]
 # FP64-pipe instructions per lattice update of step_kernel<double> (ncu: the FP64 pipe was
 # 87.6 % busy, 598 instructions per node; profiles/step_kernel_f64_pull_hit128.md) and the
@@ -222,7 +225,8 @@ def run_box(w, steps, warmup, want_kernel_time=True):
     import torch
     from paper_1507_02518_gb300 import lb
     rho, u = make_field(w)
-    lat = lb.Lattice(w["n"], nu=w["nu"], storage=w["storage"], scheme=w["scheme"])
+    lat = lb.Lattice(w["n"], nu=w["nu"], storage=w["storage"], scheme=w["scheme"],
+                     variant=w.get("variant", "d+t+q"))
     st = lat.stream
     lat.init_field(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
     del rho, u
