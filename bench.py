@@ -48,6 +48,10 @@ VARIANTS = [
      "storage": "f16", "scheme": "aa", "diag_every": 50, "steps": 200},
     {"name": "batch96_f32_pull", "field": "batch", "nbox": 96, "storage": "f32",
      "scheme": "pull", "steps": 200},
+    {"name": "hit768_f16_aa", "n": 768, "field": "spectrum", "k0": 4.0, "urms": 0.05,
+     "nu": 2e-5, "seed": 1, "storage": "f16", "scheme": "aa", "diag_every": 50, "steps": 100},
+    {"name": "hit768_f32_aa", "n": 768, "field": "spectrum", "k0": 4.0, "urms": 0.05,
+     "nu": 2e-5, "seed": 1, "storage": "f32", "scheme": "aa", "diag_every": 50, "steps": 100},
     {"name": "hit256_f32_pull_central", "n": 256, "field": "spectrum", "k0": 4.0, "urms": 0.04,
      "nu": 2e-4, "seed": 1, "storage": "f32", "scheme": "pull", "diag_every": 50, "steps": 400,
      "variant": "cd+ct+cq"},
@@ -211,8 +215,12 @@ class ClockSampler:
 
 def make_field(w):
     from paper_1507_02518_gb300 import workloads
+    if w["field"] == "spectrum" and w["n"] > 512:
+        return workloads.random_spectrum_device(w["n"], w["k0"], w["urms"], w["seed"])
     if w["field"] == "spectrum":
         return workloads.random_spectrum(w["n"], w["k0"], w["urms"], w["seed"])
+    if w["field"] == "kida" and w["n"] > 512:
+        return workloads.kida_device(w["n"], w["U0"])
     if w["field"] == "kida":
         return workloads.kida(w["n"], w["U0"])
     if w["field"] == "tgv":
@@ -228,8 +236,10 @@ def run_box(w, steps, warmup, want_kernel_time=True):
     lat = lb.Lattice(w["n"], nu=w["nu"], storage=w["storage"], scheme=w["scheme"],
                      variant=w.get("variant", "d+t+q"))
     st = lat.stream
-    lat.init_field(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
-    del rho, u
+    u_dev = u if isinstance(u, torch.Tensor) else torch.from_numpy(u).cuda()
+    lat.init_field(None, u_dev)
+    del rho, u, u_dev
+    torch.cuda.empty_cache()
     lat.step(warmup)
     torch.cuda.synchronize()
     every = w.get("diag_every", 0) or steps

@@ -99,6 +99,58 @@ def random_spectrum(n: int, k0: float, urms: float, seed: int, dtype=np.float64)
     return np.ones((n, n, n)), u.astype(dtype, copy=False)
 
 
+def random_spectrum_device(n: int, k0: float, urms: float, seed: int, device="cuda"):
+    """The recipe of random_spectrum generated on a GPU with torch (float64), for boxes whose
+    host generation would be slow (768^3). Same spectrum, projection and scaling; the white
+    noise comes from torch's generator seeded with ``seed``, so the field differs from the
+    numpy version of the same seed. Returns (None, u[3, n, n, n]) on ``device`` (density 1).
+    """
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    kf = torch.fft.fftfreq(n, d=1.0 / n, dtype=torch.float64, device=device)
+    kr = torch.fft.rfftfreq(n, d=1.0 / n, dtype=torch.float64, device=device)
+    KZ = kf.view(n, 1, 1)
+    KY = kf.view(1, n, 1)
+    KX = kr.view(1, 1, -1)
+    K2 = KX * KX + KY * KY + KZ * KZ
+    K = torch.sqrt(K2)
+    amp = K * torch.exp(-((K / k0) ** 2))
+    nyq = n // 2
+    mask = (KX.abs() == nyq) | (KY.abs() == nyq) | (KZ.abs() == nyq) | (K == 0)
+    amp = torch.where(mask, torch.zeros_like(amp), amp)
+    a = []
+    for _ in range(3):
+        noise = torch.randn((n, n, n), generator=gen, dtype=torch.float64, device=device)
+        a.append(torch.fft.rfftn(noise) * amp)
+        del noise
+    safe = torch.where(K2 > 0, K2, torch.ones_like(K2))
+    kdota = (KX * a[0] + KY * a[1] + KZ * a[2]) / safe
+    a[0] = a[0] - KX * kdota
+    a[1] = a[1] - KY * kdota
+    a[2] = a[2] - KZ * kdota
+    del kdota, K, K2, amp, mask, safe
+    u = torch.empty((3, n, n, n), dtype=torch.float64, device=device)
+    for c in range(3):
+        u[c] = torch.fft.irfftn(a[c], s=(n, n, n))
+        a[c] = None
+    rms = math.sqrt(float((u * u).sum()) / (3.0 * n ** 3))
+    u *= urms / rms
+    return None, u
+
+
+def kida_device(n: int, U0: float = 0.05, device="cuda"):
+    """eq:kida on a GPU with torch (float64); returns (None, u[3, n, n, n]) on ``device``."""
+    import torch
+    x = torch.arange(n, dtype=torch.float64, device=device) * (2.0 * math.pi / n)
+    X, Y, Z = x.view(1, 1, n), x.view(1, n, 1), x.view(n, 1, 1)
+    u = torch.empty((3, n, n, n), dtype=torch.float64, device=device)
+    u[0] = U0 * torch.sin(X) * (torch.cos(3 * Y) * torch.cos(Z) - torch.cos(Y) * torch.cos(3 * Z))
+    u[1] = U0 * torch.sin(Y) * (torch.cos(3 * Z) * torch.cos(X) - torch.cos(Z) * torch.cos(3 * X))
+    u[2] = U0 * torch.sin(Z) * (torch.cos(3 * X) * torch.cos(Y) - torch.cos(X) * torch.cos(3 * Y))
+    return None, u
+
+
 def population_noise(nx: int, ny: int, nz: int, seed: int):
     """Uniform noise in [-1, 1] shaped like a population field, [27, z, y, x]."""
     rng = np.random.default_rng(seed)

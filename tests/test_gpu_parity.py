@@ -501,8 +501,9 @@ def test_batch_autotune_and_graph_replay(kbc):
 
 # ------------------------------------------------------------------ full-size sampled parity
 
-def _sampled_step_check(lat, nsample, tol, rng):
-    """Compare f(t+1) at sampled nodes with the oracle applied to the GPU's f(t) (FP64 copy)."""
+def _sampled_step_check(lat, nsample, tol, rng, half=False):
+    """Compare f(t+1) at sampled nodes with the oracle applied to the GPU's f(t) (FP64 copy).
+    half: the result is stored in FP16, so allow one half-ulp of (f - W)/W on top of tol."""
     import torch
     nz, ny, nx = lat.shape
     P = lat.P
@@ -521,12 +522,18 @@ def _sampled_step_check(lat, nsample, tol, rng):
     lat.step(1)
     lb.lb_get_populations(lat.ctx, dev.data_ptr(), True)
     fout = dev[:, torch.from_numpy(idx).cuda()].cpu().numpy()   # [pop, sample]
+    del dev
+    torch.cuda.empty_cache()
     beta = lat.beta
     worst = 0.0
     for s in range(nsample):
         for i in range(27):
             post, _, _ = oracle.collide(fin[:, i, s], beta)
-            worst = max(worst, abs(post[i] - fout[i, s]))
+            err = abs(post[i] - fout[i, s])
+            if half:
+                h = np.float16((post[i] - W[i]) / W[i])
+                err = max(0.0, err - W[i] * float(np.spacing(np.abs(h))))
+            worst = max(worst, err)
     assert worst <= tol, worst
     return worst
 
@@ -544,3 +551,24 @@ def test_full_size_256cubed_fp32_sampled_parity(kbc):
     assert abs(d1["mass"] - d0["mass"]) / d0["mass"] < 1e-7
     rng = np.random.default_rng(0)
     _sampled_step_check(lat, 48, FP32_STEP_TOL, rng)
+
+
+def test_max_size_768cubed_fp16_aa_sampled_parity(kbc):
+    """The largest configuration (768^3 = 453 M nodes, FP16 AA in place, 24.5 GB): 64-bit plane
+    offsets and the in-place odd/even steps at full size. Kida field generated on the GPU."""
+    import torch
+    n, nu = 768, 2e-5
+    _, u = workloads.kida_device(n, 0.05)
+    lat = lb.Lattice(n, nu=nu, storage="f16", scheme="aa")
+    lat.init_field(None, u)
+    del u
+    torch.cuda.empty_cache()
+    d0 = lat.diagnostics()
+    assert d0["kinetic_energy"] == pytest.approx(3 * 0.05 ** 2 / 8, rel=2e-3)
+    lat.step(3)
+    d1 = lat.diagnostics()
+    assert d1["nonfinite_count"] == 0
+    assert abs(d1["mass"] - d0["mass"]) / d0["mass"] < 1e-6
+    rng = np.random.default_rng(1)
+    _sampled_step_check(lat, 24, FP32_STEP_TOL, rng, half=True)     # the odd step t = 3 -> 4
+    _sampled_step_check(lat, 24, FP32_STEP_TOL, rng, half=True)     # the even step t = 4 -> 5
