@@ -450,8 +450,8 @@ def main_ours(args, rank, world, local):
                         "frac_hbm": roofline(v["storage"], kml, peak, peak_kind)["frac"],
                         "kinetic_energy": d["kinetic_energy"], "gamma_mean": d["gamma_mean"]}
                     if v["storage"] == "f64":
-                        clk = clk_mhz or 2070.0
-                        pipe_peak = FP64_PIPE_PER_SM_PER_CYCLE * sms * clk * 1e6
+                        sm_mhz = clk_mhz or 2070.0
+                        pipe_peak = FP64_PIPE_PER_SM_PER_CYCLE * sms * sm_mhz * 1e6
                         variants[v["name"]]["bound"] = "alu (FP64 pipe)"
                         variants[v["name"]]["frac_fp64_pipe"] = round(
                             kml * 1e6 * FP64_INSTR_PER_LUP / pipe_peak, 4)
