@@ -37,7 +37,8 @@ MAIN = {"name": "hit256_f32_pull", "n": 256, "field": "spectrum", "k0": 4.0, "ur
         "nu": 2e-4, "seed": 1, "storage": "f32", "scheme": "pull", "diag_every": 50}
 VARIANTS = [
     {"name": "hit256_f64_pull", "n": 256, "field": "spectrum", "k0": 4.0, "urms": 0.04,
-     "nu": 2e-4, "seed": 1, "storage": "f64", "scheme": "pull", "diag_every": 50, "steps": 100},
+     "nu": 2e-4, "seed": 1, "storage": "f64", "scheme": "pull", "diag_every": 50, "steps": 100,
+     "gap": True},
     {"name": "hit256_f32_aa", "n": 256, "field": "spectrum", "k0": 4.0, "urms": 0.04,
      "nu": 2e-4, "seed": 1, "storage": "f32", "scheme": "aa", "diag_every": 50, "steps": 400},
     {"name": "hit256_f16_aa", "n": 256, "field": "spectrum", "k0": 4.0, "urms": 0.04,
@@ -55,6 +56,14 @@ VARIANTS = [
     {"name": "hit256_f32_pull_central", "n": 256, "field": "spectrum", "k0": 4.0, "urms": 0.04,
      "nu": 2e-4, "seed": 1, "storage": "f32", "scheme": "pull", "diag_every": 50, "steps": 400,
      "variant": "cd+ct+cq"},
+    # exact stabilizer (Newton root of eq:result1 at every node and step) and its gap to the
+    # estimate eq:result21 on the final state
+    {"name": "hit128_f64_pull_exact", "n": 128, "field": "spectrum", "k0": 4.0, "urms": 0.04,
+     "nu": 2e-4, "seed": 1, "storage": "f64", "scheme": "pull", "diag_every": 50, "steps": 50,
+     "gamma": "exact", "gap": True},
+    {"name": "hit128_f32_pull_exact", "n": 128, "field": "spectrum", "k0": 4.0, "urms": 0.04,
+     "nu": 2e-4, "seed": 1, "storage": "f32", "scheme": "pull", "diag_every": 50, "steps": 100,
+     "gamma": "exact", "gap": True},
 ]
 # FP64-pipe instructions per lattice update of step_kernel<double> (ncu: the FP64 pipe was
 # 87.6 % busy, 598 instructions per node; profiles/step_kernel_f64_pull_hit128.md) and the
@@ -235,7 +244,7 @@ def run_box(w, steps, warmup, want_kernel_time=True):
     from paper_1507_02518_gb300 import lb
     rho, u = make_field(w)
     lat = lb.Lattice(w["n"], nu=w["nu"], storage=w["storage"], scheme=w["scheme"],
-                     variant=w.get("variant", "d+t+q"))
+                     variant=w.get("variant", "d+t+q"), gamma=w.get("gamma", "estimate"))
     st = lat.stream
     u_dev = u if isinstance(u, torch.Tensor) else torch.from_numpy(u).cuda()
     lat.init_field(None, u_dev)
@@ -450,7 +459,14 @@ def main_ours(args, rank, world, local):
                         "MLUPS": round(mlups, 1), "kernel_MLUPS": round(kml, 1), "steps": vs,
                         "frac_hbm": roofline(v["storage"], kml, peak, peak_kind)["frac"],
                         "kinetic_energy": d["kinetic_energy"], "gamma_mean": d["gamma_mean"]}
-                    if v["storage"] == "f64":
+                    if v.get("gap"):
+                        gp = r["lat"].stabilizer_gap()
+                        variants[v["name"]]["gamma_gap"] = {
+                            k: gp[k] for k in ("mean_abs", "max_abs", "mean_estimate",
+                                               "mean_exact", "unconverged", "skipped")}
+                    if v.get("gamma") == "exact":
+                        variants[v["name"]]["bound"] = "alu (Newton iterations)"
+                    elif v["storage"] == "f64":
                         sm_mhz = clk_mhz or 2070.0
                         pipe_peak = FP64_PIPE_PER_SM_PER_CYCLE * sms * sm_mhz * 1e6
                         variants[v["name"]]["bound"] = "alu (FP64 pipe)"

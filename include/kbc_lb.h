@@ -54,9 +54,14 @@ enum {
   LB_S_D = 0, LB_S_DT = 1, LB_S_DQ = 2, LB_S_DTQ = 3,
   LB_S_CD = 4, LB_S_CDT = 5, LB_S_CDQ = 6, LB_S_CDTQ = 7
 };
-/* Stabilizer: eq:result21 (the method), or the fixed special cases named in Sec. KBC:
- * gamma = 2 (LBGK) and gamma = 1/beta (regularized LB). */
-enum { LB_GAMMA_ESTIMATE = 0, LB_GAMMA_LBGK = 1, LB_GAMMA_RLB = 2 };
+/* Stabilizer: eq:result21 (the method), the fixed special cases named in Sec. KBC
+ * (gamma = 2, LBGK; gamma = 1/beta, regularized LB), or LB_GAMMA_EXACT: per node the root
+ * gamma* of the entropy condition eq:result1, by a damped Newton iteration started from
+ * eq:result21 (at most 50 iterations in FP64, 20 in FP32; each step halved until every
+ * logarithm's argument stays positive; nodes where <dh|dh> falls under the guard keep
+ * gamma = 2). LB_GAMMA_EXACT runs in the one-node-per-thread direct kernel only and is not
+ * available to batches. */
+enum { LB_GAMMA_ESTIMATE = 0, LB_GAMMA_LBGK = 1, LB_GAMMA_RLB = 2, LB_GAMMA_EXACT = 3 };
 /* Storage of the populations in device memory; collision arithmetic is FP64 for LB_F64 and
  * FP32 otherwise. All three store the shift f_i - W_i; LB_F16 stores (f_i - W_i)/W_i in
  * IEEE half precision, rounded to nearest even. */
@@ -75,7 +80,8 @@ typedef struct {
 } lb_config;
 
 /* Diagnostics of Sec. "Numerical Simulations" at the current time t. Averages <.> are over
- * nodes; u' = u - <u>; gradients are second-order central differences. */
+ * nodes; u' = u - <u>; gradients are central differences of order grad_order: 2 (the
+ * default, as for the paper's enstrophy curves) or 8 (Table 2), see lb_set_diag_order. */
 typedef struct {
   int64_t step;             /* t */
   int64_t nodes;            /* P */
@@ -89,7 +95,26 @@ typedef struct {
   int64_t nonfinite_count;  /* nodes whose rho or u is NaN/Inf */
   int64_t den_guard_count;  /* nodes where <dh|dh> fell under the guard (gamma set to 2),
                                counted over the same collision as gamma_mean */
+  int32_t grad_order;       /* 2 or 8 */
+  int32_t reserved;
+  double dudx2;             /* <(d u'_x / d x)^2> */
+  double skewness[4];       /* longitudinal skewness factors S_11^n, n = 3..6 (Table 2):
+                               (-1)^n <(d u'_x/d x)^n> <(d u'_x/d x)^2>^(-n/2) */
 } lb_diag;
+
+/* Gap between the stabilizer estimate eq:result21 and the exact root gamma* of eq:result1,
+ * both evaluated on the collision inputs of the current state f(t) (Sec. KBC). Averages are
+ * over the evaluated nodes; nodes under the <dh|dh> guard or holding NaN/Inf are skipped. */
+typedef struct {
+  int64_t step;          /* t */
+  int64_t nodes;         /* nodes evaluated */
+  double mean_abs;       /* <|gamma_est - gamma*|> */
+  double max_abs;        /* max |gamma_est - gamma*| */
+  double mean_estimate;  /* <gamma_est> */
+  double mean_exact;     /* <gamma*> */
+  int64_t unconverged;   /* nodes where the Newton iteration stopped before converging */
+  int64_t skipped;       /* nodes skipped (guard or non-finite) */
+} lb_gap;
 
 typedef struct lb_ctx lb_ctx;
 
@@ -115,6 +140,24 @@ const char *lb_last_error(const lb_ctx *ctx);
  * Host inputs are copied through the staging area in chunks; |u_a| < 1 is required. */
 lb_status lb_init_field(lb_ctx *ctx, const double *rho, const double *u, int on_device);
 
+/* Consistent initial state (Sec. "Numerical Simulations": the initial density and higher
+ * moments come from an iteration run to steady state beforehand, after Mei et al.). Sets
+ * f = f_eq(1, u0), then iterates
+ *     f <- S[ f - 2 beta_pre (f - f_eq(rho(f), u0)) ],   beta_pre = 1/(6 nu_pre + 1),
+ * (S: propagation) with the velocity of the equilibrium held at u0 while the density evolves.
+ * Every 32 iterations (and after the last) the largest change of rho over the last iteration
+ * is measured, on rho - 1 rounded to FP32; the loop stops when it is <= tol (a negative tol
+ * runs max_iters) or after max_iters iterations, rounded up to an even count. The result is
+ * the state at t = 0; lb_diagnostics has no gamma until the next lb_step.
+ *   u0        FP64 [3][P], host (copied in chunks) or device (on_device != 0)
+ *   nu_pre    > 0, the pre-solve's own relaxation (1/6 relaxes fully to f_eq each iteration)
+ *   iters     iterations run (may be NULL);  residual  the last measured change (may be NULL;
+ *             NaN if max_iters is 0)
+ * Uses the diagnostics work area and the gamma field as scratch. Synchronises. Returns
+ * LB_ERR_NONFINITE if the iteration produced NaN/Inf. */
+lb_status lb_presolve(lb_ctx *ctx, const double *u0, int on_device, double nu_pre,
+                      int64_t max_iters, double tol, int64_t *iters, double *residual);
+
 /* Advance n >= 0 time steps (eq:Egeneral with the KBC collision). Asynchronous. The last of
  * the n collisions also records gamma per node for lb_diagnostics. */
 lb_status lb_step(lb_ctx *ctx, int64_t n);
@@ -125,6 +168,30 @@ lb_status lb_moments(lb_ctx *ctx, double *rho, double *u, int on_device);
 /* Fill *out for the current state. Synchronises. Returns LB_ERR_NONFINITE (with *out filled)
  * if any node is NaN/Inf. */
 lb_status lb_diagnostics(lb_ctx *ctx, lb_diag *out);
+
+/* Order (2 or 8) of the central differences lb_diagnostics uses for velocity gradients:
+ * du/dx = sum_k c_k (u(x + k) - u(x - k)), c = 1/2 (order 2) or 4/5, -1/5, 4/105, -1/280
+ * (order 8). Default 2. */
+lb_status lb_set_diag_order(lb_ctx *ctx, int32_t order);
+
+/* Kinetic-energy spectrum of the current state (Sec. "Numerical Simulations": E(kappa) with
+ * k = integral of E; D(kappa) = 2 nu kappa^2 E(kappa)). Cubic boxes (nx = ny = nz = N) only.
+ *   E[m], m = 0..nbins-1 (host, caller-owned): the sum over integer wave vectors n != 0 with
+ *        rint(|n|) = m of 1/2 |u_hat(n)|^2, u_hat(n) = (1/P) sum_x u(x) e^{-2 pi i n.x/N}; shell m
+ *        holds kappa = 2 pi m / N, sum_m E[m] = k when nbins > sqrt(3) N / 2 (higher shells are
+ *        dropped otherwise). E[0] = 0 (the mean flow is not part of u').
+ *   work  device buffer of lb_spectrum_work_bytes(ctx, nbins) bytes, 256-byte aligned, owned
+ *         by the caller (FFT of one velocity component, the FFT work area, block histograms).
+ * The velocity is the one lb_diagnostics uses (collision precision); the 3D real-to-complex
+ * FFTs are cuFFT's (its plan holds a small internal allocation for the duration of the call).
+ * 1 <= nbins <= 6144. Synchronises. LB_ERR_UNSUPPORTED for non-cubic boxes. */
+size_t lb_spectrum_work_bytes(lb_ctx *ctx, int32_t nbins);
+lb_status lb_spectrum(lb_ctx *ctx, void *work, size_t work_bytes, int32_t nbins, double *E);
+
+/* Fill *out with the stabilizer gap of the current state (NaN averages when no node was
+ * evaluated). Does not advance t or touch the populations; uses the diagnostics work area.
+ * Synchronises. Arithmetic in the collision precision of the storage (FP64 for LB_F64). */
+lb_status lb_stabilizer_gap(lb_ctx *ctx, lb_gap *out);
 
 /* Canonical pre-collision populations f[27][P] (FP64, caller-owned) at the current time t,
  * whatever the scheme and step parity. Synchronises. */

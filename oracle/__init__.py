@@ -11,8 +11,9 @@ Field layout: ``f[27, nz, ny, nx]`` (plane i contiguous, x fastest), velocity in
 Parity pins: every function here is pinned by ``tests/test_oracle_*.py`` against properties the
 paper and the mathematics fix (conservation, fixed point, LBGK/RLB limits, the moment-basis
 inverse, cube symmetry, entropy maximum, analytic decay rates, closed-form diagnostics). The
-exact-stabilizer root (``gamma_exact``) is pinned only through the entropy-maximum property and
-its limit toward eq:result21.
+exact-stabilizer root (``gamma_exact``) is pinned by a bracketing root of the entropy
+derivative and its limit toward eq:result21; the density pre-solve (``presolve``) by mass
+conservation, its fixed points and the closed-form pressure of the Taylor-Green vortex.
 """
 from __future__ import annotations
 
@@ -81,10 +82,12 @@ def lib():
             L.orc_collide_field.argtypes = [i32, i32, i32, vp, d, ctypes.c_int, ctypes.c_int, vp]
             L.orc_init_equilibrium.argtypes = [i32, i32, i32, vp, vp, vp]
             L.orc_macroscopic.argtypes = [i32, i32, i32, vp, vp, vp]
-            L.orc_diagnostics.argtypes = [i32, i32, i32, vp, vp, d, vp]
+            L.orc_diagnostics.argtypes = [i32, i32, i32, vp, vp, d, ctypes.c_int, vp]
             L.orc_run.restype = i64
             L.orc_run.argtypes = [i32, i32, i32, vp, vp, i64, d, ctypes.c_int, ctypes.c_int,
                                        vp]
+            L.orc_presolve.restype = i64
+            L.orc_presolve.argtypes = [i32, i32, i32, vp, vp, vp, d, i64, d, vp]
             L.orc_num_threads.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -243,14 +246,59 @@ def macroscopic(f):
     return rho, u
 
 
-def diagnostics(rho, u, nu):
-    """dict(mass, momentum[3], kinetic_energy, enstrophy, dissipation) from rho, u."""
+def diagnostics(rho, u, nu, order=2):
+    """dict(mass, momentum[3], kinetic_energy, enstrophy, dissipation, dudx2, skewness[S3..S6])
+    from rho, u; derivatives by central differences of order 2 or 8."""
+    assert order in (2, 8)
     rho, u = _f64(rho), _f64(u)
     nz, ny, nx = rho.shape
-    out = np.zeros(8)
-    lib().orc_diagnostics(nx, ny, nz, _p(rho), _p(u), float(nu), _p(out))
+    out = np.zeros(13)
+    lib().orc_diagnostics(nx, ny, nz, _p(rho), _p(u), float(nu), int(order), _p(out))
     return {"mass": out[0], "momentum": out[1:4].copy(), "kinetic_energy": out[4],
-            "enstrophy": out[5], "dissipation": out[6]}
+            "enstrophy": out[5], "dissipation": out[6], "dudx2": out[8],
+            "skewness": out[9:13].copy()}
+
+
+def spectrum(u, nbins):
+    """Shell-summed kinetic-energy spectrum of u' = u - <u> on a periodic N^3 grid (Sec.
+    "Numerical Simulations": E(kappa) with k = integral of E, D(kappa) = 2 nu kappa^2 E).
+
+    E[m] = sum over integer wave vectors n != 0 with round(|n|) == m of 1/2 |u_hat(n)|^2,
+    u_hat(n) = (1/P) sum_x u(x) exp(-2 pi i n.x / N), so that sum_m E[m] = k (Parseval).
+    Shell m holds kappa = 2 pi m / N. A plain full complex FFT per component and a loop-free
+    binning; numpy's FFT is the library step."""
+    u = _f64(u)
+    _, nz, ny, nx = u.shape
+    assert nx == ny == nz, "cubic boxes only"
+    n = nx
+    P = n ** 3
+    idx = np.fft.fftfreq(n, 1.0 / n)                 # 0, 1, ..., -1 (integers)
+    NZ, NY, NX = np.meshgrid(idx, idx, idx, indexing="ij")
+    shell = np.rint(np.sqrt(NX ** 2 + NY ** 2 + NZ ** 2)).astype(np.int64)
+    e = np.zeros((nz, ny, nx))
+    for a in range(3):
+        uh = np.fft.fftn(u[a]) / P
+        e += 0.5 * np.abs(uh) ** 2
+    e[0, 0, 0] = 0.0                                  # the mean flow is not part of u'
+    E = np.zeros(nbins)
+    keep = shell < nbins
+    np.add.at(E, shell[keep], e[keep])
+    return E
+
+
+def presolve(u0, beta_pre, max_iters, tol=-1.0, f=None):
+    """Consistent initial state: the iteration of ``orc_presolve`` from f (default
+    f_eq(1, u0)). Returns (f, iterations run, last change of rho)."""
+    u0 = _f64(u0)
+    _, nz, ny, nx = u0.shape
+    if f is None:
+        f = init_equilibrium(np.ones((nz, ny, nx)), u0)
+    f = _f64(f).copy()
+    fb = np.empty_like(f)
+    res = ctypes.c_double()
+    it = lib().orc_presolve(nx, ny, nz, _p(f), _p(fb), _p(u0), float(beta_pre), int(max_iters),
+                            float(tol), ctypes.byref(res))
+    return f, int(it), res.value
 
 
 def run(f, nsteps, beta_, variant=S_DTQ, gamma_mode=GAMMA_ESTIMATE, want_gamma=False):

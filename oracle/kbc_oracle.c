@@ -456,9 +456,18 @@ void orc_macroscopic(int32_t nx, int32_t ny, int32_t nz, const double *f, double
  * out[4] = k = 1/2 <u'.u'>,  u' = u - <u>,
  * out[5] = Omega = 1/2 <|curl u'|^2>,
  * out[6] = epsilon = 1/2 nu <(d_b u'_a + d_a u'_b)^2>,
- * derivatives by second-order central differences on the periodic grid. */
+ * out[7] = P, out[8] = <(d u'_x / d x)^2>,
+ * out[9..12] = longitudinal skewness factors S_11^n, n = 3..6:
+ *              (-1)^n <(d u'_x/d x)^n> <(d u'_x/d x)^2>^(-n/2),
+ * derivatives by central differences of order 2 (the figures) or 8 (Table 2) on the periodic
+ * grid: d u / d x = sum_k c_k (u(x + k) - u(x - k)),
+ * order 2: c_1 = 1/2;  order 8: c = 4/5, -1/5, 4/105, -1/280. */
 void orc_diagnostics(int32_t nx, int32_t ny, int32_t nz, const double *rho, const double *u,
-                     double nu, double *out) {
+                     double nu, int order, double *out) {
+  static const double c2[1] = {0.5};
+  static const double c8[4] = {4.0 / 5.0, -1.0 / 5.0, 4.0 / 105.0, -1.0 / 280.0};
+  const double *coef = order == 8 ? c8 : c2;
+  const int K = order == 8 ? 4 : 1;
   const int64_t P = (int64_t)nx * ny * nz;
   double mass = 0.0, mom[3] = {0, 0, 0}, mean[3] = {0, 0, 0};
   for (int64_t n = 0; n < P; ++n) {
@@ -469,7 +478,7 @@ void orc_diagnostics(int32_t nx, int32_t ny, int32_t nz, const double *rho, cons
     }
   }
   for (int a = 0; a < 3; ++a) mean[a] /= (double)P;
-  double ke = 0.0, ens = 0.0, dis = 0.0;
+  double ke = 0.0, ens = 0.0, dis = 0.0, pw[7] = {0, 0, 0, 0, 0, 0, 0};
   const int64_t dims[3] = {nx, ny, nz};
   for (int64_t z = 0; z < nz; ++z)
     for (int64_t y = 0; y < ny; ++y)
@@ -477,14 +486,17 @@ void orc_diagnostics(int32_t nx, int32_t ny, int32_t nz, const double *rho, cons
         const int64_t n = x + nx * (y + ny * z);
         const int64_t c[3] = {x, y, z};
         double g[3][3]; /* g[a][b] = d u_a / d x_b */
-        for (int b = 0; b < 3; ++b) {
-          int64_t cp[3] = {c[0], c[1], c[2]}, cm[3] = {c[0], c[1], c[2]};
-          cp[b] = wrap(c[b] + 1, dims[b]);
-          cm[b] = wrap(c[b] - 1, dims[b]);
-          const int64_t np = cp[0] + nx * (cp[1] + ny * cp[2]);
-          const int64_t nm = cm[0] + nx * (cm[1] + ny * cm[2]);
-          for (int a = 0; a < 3; ++a) g[a][b] = (u[a * P + np] - u[a * P + nm]) / 2.0;
-        }
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) g[a][b] = 0.0;
+        for (int b = 0; b < 3; ++b)
+          for (int k = 1; k <= K; ++k) {
+            int64_t cp[3] = {c[0], c[1], c[2]}, cm[3] = {c[0], c[1], c[2]};
+            cp[b] = wrap(c[b] + k, dims[b]);
+            cm[b] = wrap(c[b] - k, dims[b]);
+            const int64_t np = cp[0] + nx * (cp[1] + ny * cp[2]);
+            const int64_t nm = cm[0] + nx * (cm[1] + ny * cm[2]);
+            for (int a = 0; a < 3; ++a) g[a][b] += coef[k - 1] * (u[a * P + np] - u[a * P + nm]);
+          }
         for (int a = 0; a < 3; ++a) {
           const double up = u[a * P + n] - mean[a];
           ke += up * up;
@@ -496,6 +508,11 @@ void orc_diagnostics(int32_t nx, int32_t ny, int32_t nz, const double *rho, cons
             const double sab = g[a][b] + g[b][a];
             dis += sab * sab;
           }
+        double q = 1.0;
+        for (int m = 1; m <= 6; ++m) {
+          q *= g[0][0];
+          pw[m] += q;
+        }
       }
   out[0] = mass;
   for (int a = 0; a < 3; ++a) out[1 + a] = mom[a];
@@ -503,6 +520,10 @@ void orc_diagnostics(int32_t nx, int32_t ny, int32_t nz, const double *rho, cons
   out[5] = 0.5 * ens / (double)P;
   out[6] = 0.5 * nu * dis / (double)P;
   out[7] = (double)P;
+  const double m2 = pw[2] / (double)P;
+  out[8] = m2;
+  for (int m = 3; m <= 6; ++m)
+    out[9 + m - 3] = (m % 2 ? -1.0 : 1.0) * (pw[m] / (double)P) / pow(m2, 0.5 * m);
 }
 
 /* nsteps of eq:Egeneral on the pre-collision field f(t): collide every node (right-hand
@@ -523,6 +544,53 @@ int64_t orc_run(int32_t nx, int32_t ny, int32_t nz, double *fa, double *fb, int6
   }
   if (a != fa) memcpy(fa, a, (size_t)(27 * P) * sizeof(double));
   return guarded;
+}
+
+/* Consistent initial density and higher moments (Sec. "Numerical Simulations", following
+ * Mei et al.): the lattice Boltzmann iteration with the velocity held at the prescribed u0,
+ *   f <- S[ f - 2 beta_pre (f - f_eq(rho(f), u0)) ],   S = propagation (orc_stream),
+ * whose density relaxes to the steady state of its mass balance. After each iteration the
+ * change max_x |rho^{n+1}(x) - rho^n(x)| is measured; the loop stops after the first
+ * iteration whose change is <= tol, or after max_iters. Returns the iterations run;
+ * *residual = the last change (NaN when none was run). fb is scratch of the size of f. */
+int64_t orc_presolve(int32_t nx, int32_t ny, int32_t nz, double *f, double *fb, const double *u0,
+                     double beta_pre, int64_t max_iters, double tol, double *residual) {
+  const int64_t P = (int64_t)nx * ny * nz;
+  double *rho_old = (double *)malloc((size_t)P * sizeof(double));
+  double res = NAN;
+  int64_t it = 0;
+  for (int64_t n = 0; n < P; ++n) {
+    double r = 0.0;
+    for (int i = 0; i < 27; ++i) r += f[i * P + n];
+    rho_old[n] = r;
+  }
+  while (it < max_iters) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int64_t n = 0; n < P; ++n) {
+      double rho = 0.0, feq[27];
+      for (int i = 0; i < 27; ++i) rho += f[i * P + n];
+      const double un[3] = {u0[n], u0[P + n], u0[2 * P + n]};
+      orc_equilibrium(rho, un, feq);
+      for (int i = 0; i < 27; ++i) f[i * P + n] -= 2.0 * beta_pre * (f[i * P + n] - feq[i]);
+    }
+    orc_stream(nx, ny, nz, f, fb);
+    memcpy(f, fb, (size_t)(27 * P) * sizeof(double));
+    ++it;
+    res = 0.0;
+    for (int64_t n = 0; n < P; ++n) {
+      double r = 0.0;
+      for (int i = 0; i < 27; ++i) r += f[i * P + n];
+      const double ch = fabs(r - rho_old[n]);
+      if (!(ch <= res)) res = ch;    /* NaN propagates */
+      rho_old[n] = r;
+    }
+    if (res <= tol) break;
+  }
+  free(rho_old);
+  if (residual) *residual = res;
+  return it;
 }
 
 int orc_num_threads(void) {

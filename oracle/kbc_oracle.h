@@ -64,9 +64,12 @@ void   orc_init_equilibrium(int32_t nx, int32_t ny, int32_t nz, const double *rh
 void   orc_macroscopic(int32_t nx, int32_t ny, int32_t nz, const double *f, double *rho,
                        double *u);
 void   orc_diagnostics(int32_t nx, int32_t ny, int32_t nz, const double *rho, const double *u,
-                       double nu, double *out /*8*/);
+                       double nu, int order, double *out /*13*/);
 int64_t orc_run(int32_t nx, int32_t ny, int32_t nz, double *fa, double *fb, int64_t nsteps,
                 double beta, int variant, int gamma_mode, double *gamma_field);
+int64_t orc_presolve(int32_t nx, int32_t ny, int32_t nz, double *f, double *fb,
+                     const double *u0, double beta_pre, int64_t max_iters, double tol,
+                     double *residual);
 int    orc_num_threads(void);
 
 #ifdef __cplusplus

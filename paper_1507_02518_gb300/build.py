@@ -17,7 +17,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkbc.so")
-SOURCES = ["lb_api.cu", "kbc_f64.cu", "kbc_f32.cu", "kbc_f16.cu", "lb_noalloc.cu"]
+SOURCES = ["lb_api.cu", "kbc_f64.cu", "kbc_f32.cu", "kbc_f16.cu", "lb_noalloc.cu",
+           "kbc_spectrum.cu"]
+LIBS = ["-lcufft"]          # the spectrum's 3D FFTs
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -70,7 +72,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for _, log in results:
             sys.stdout.write(log)
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results]
+    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + LIBS
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))

@@ -116,7 +116,7 @@ template <typename R> struct Guard;
 template <> struct Guard<double> { static constexpr double den = 1e-300; };
 template <> struct Guard<float> { static constexpr float den = 1e-30f; };
 
-enum { GAMMA_ESTIMATE = 0, GAMMA_LBGK = 1, GAMMA_RLB = 2 };
+enum { GAMMA_ESTIMATE = 0, GAMMA_LBGK = 1, GAMMA_RLB = 2, GAMMA_EXACT = 3 };
 
 struct CollideParams {
   double beta;      // relaxation parameter of eq:Egeneral
@@ -221,11 +221,78 @@ template <> struct Ar<double> {
   static __device__ __forceinline__ void set_lane(double& a, int, double v) { a = v; }
 };
 
+// ------------------------------------------------------------------ exact stabilizer
+// The root gamma* of eq:result1,
+//   g(gamma) = sum_i dh_i ln(1 + ((1 - beta gamma) dh_i - (2 beta - 1) ds_i) / f_eq_i) = 0,
+// the critical point of the post-collision entropy along gamma (Sec. KBC). g is strictly
+// decreasing where every logarithm is defined: g'(gamma) = -beta sum_i dh_i^2 / (f_eq_i (1+x_i)).
+// Newton's method from the estimate eq:result21, each step halved until every argument
+// 1 + x_i stays positive; bounded iteration counts. With a_i = dh_i - (2 beta - 1) ds_i,
+// x_i = (a_i - beta gamma dh_i) / f_eq_i and 1/f_eq_i = rx[a] ry[b] rz[c].
+template <typename T> struct NewtonLimits;
+template <> struct NewtonLimits<double> {
+  static constexpr int iters = 50;
+  static constexpr double tol = 1e-15;  // |step| <= tol (1 + |gamma|)
+};
+template <> struct NewtonLimits<float> {
+  static constexpr int iters = 20;
+  static constexpr float tol = 1e-6f;
+};
+__device__ __forceinline__ double log1p_t(double x) { return log1p(x); }
+__device__ __forceinline__ float log1p_t(float x) { return log1pf(x); }
+
+// status: 0 converged, 1 stopped where g is undefined or flat (gamma kept), 2 iteration cap
+template <typename T>
+__device__ __noinline__ T newton_gamma(const T (&dh)[27], const T (&av)[27], const T (&rx)[3],
+                                       const T (&ry)[3], const T (&rz)[3], T beta, T g,
+                                       int* status) {
+  *status = 2;
+#pragma unroll 1
+  for (int it = 0; it < NewtonLimits<T>::iters; ++it) {
+    T val = T(0), der = T(0);
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < 27; ++i) {
+      const T r = rx[i % 3] * ry[(i / 3) % 3] * rz[i / 9];
+      const T x = (av[i] - beta * g * dh[i]) * r;
+      if (!(T(1) + x > T(0))) ok = false;
+      val += dh[i] * log1p_t(x);
+      der -= beta * dh[i] * dh[i] * r / (T(1) + x);
+    }
+    if (!ok || der == T(0)) {
+      *status = 1;
+      break;
+    }
+    T step = -val / der;
+#pragma unroll 1
+    for (int tries = 0; tries < 60; ++tries) {
+      bool pos = true;
+#pragma unroll
+      for (int i = 0; i < 27; ++i) {
+        const T r = rx[i % 3] * ry[(i / 3) % 3] * rz[i / 9];
+        if (!(T(1) + (av[i] - beta * (g + step) * dh[i]) * r > T(0))) pos = false;
+      }
+      if (pos) break;
+      step *= T(0.5);
+    }
+    g += step;
+    if (fabs(step) <= NewtonLimits<T>::tol * (T(1) + fabs(g))) {
+      *status = 0;
+      break;
+    }
+  }
+  return g;
+}
+
 // One KBC collision on the shifted populations d[i] = f_i - W_i, in place (collision
 // listing of Sec. KBC); R holds one node (float, double) or two (float2). Returns gamma;
 // bit k of *guarded is set when lane k's <dh|dh> fell under the guard.
-template <typename R, bool CENTRAL = false>
-__device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, int* guarded) {
+// EXACT (one node per thread only): gamma is the root of eq:result1 found by newton_gamma()
+// from the estimate; *gamma_est receives the estimate and *newton the solver's status.
+template <typename R, bool CENTRAL = false, bool EXACT = false>
+__device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, int* guarded,
+                                     typename Ar<R>::Scalar* gamma_est = nullptr,
+                                     int* newton = nullptr) {
   using O = Ar<R>;
   using T = typename O::Scalar;
   // ---- natural moments of delta by a factorised x -> y -> z reduction (eq:natmoments)
@@ -371,6 +438,9 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, int* g
   // (listing steps 5-6): d <- d - 2 beta ds, dh kept for the gamma-dependent part
   const R nb2 = O::bc(-prec<T>(cp.two_beta, cp.two_betaf));
   R dh[27];
+  // a_i = dh_i - (2 beta - 1) ds_i, kept for the exact stabilizer only
+  [[maybe_unused]] R av[EXACT ? 27 : 1];
+  [[maybe_unused]] const R nc2 = O::sub(O::c(1.0), O::bc(prec<T>(cp.two_beta, cp.two_betaf)));
   R num = O::c(0.0), den = O::c(0.0);
   // (1 + gx)(1 + fy) - 1 for the 9 (a, b) pairs, shared by the three z levels
   R Pab[9];
@@ -460,6 +530,7 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, int* g
         rn = O::fma(t1, dsi, rn);
         rd = O::fma(t1, dhi, rd);
         dh[i] = dhi;
+        if constexpr (EXACT) av[i] = O::fma(nc2, dsi, dhi);
         d[i] = O::fma(nb2, dsi, d[i]);
       }
       cn = O::fma(ry[b], rn, cn);
@@ -492,29 +563,40 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, int* g
     O::set_lane(gamma, k, gk);
   }
   *guarded = gmask;
+  if constexpr (EXACT) {
+    static_assert(O::lanes == 1, "the exact stabilizer runs one node per thread");
+    if (gamma_est) *gamma_est = gamma;
+    int status = 1;
+    // guarded (<dh|dh> ~ 0) and non-finite nodes keep the estimate's value
+    if (!gmask && gamma == gamma && cp.gamma_mode == GAMMA_EXACT)
+      gamma = newton_gamma<T>(dh, av, rx, ry, rz, prec<T>(cp.beta, cp.betaf), gamma, &status);
+    if (newton) *newton = status;
+  }
   const R nbg = O::neg(O::mul(O::bc(prec<T>(cp.beta, cp.betaf)), gamma));
 #pragma unroll
   for (int i = 0; i < 27; ++i) d[i] = O::fma(nbg, dh[i], d[i]);
   return gamma;
 }
 
-// Equilibrium shift f_eq_i(rho, u) - W_i by the same per-axis closed form, in FP64.
-__device__ __forceinline__ void equilibrium_shift(double rho, double ux, double uy, double uz,
-                                                  double (&out)[27]) {
-  const double drho = rho - 1.0;
-  const double Rx = sqrt(1.0 + 3.0 * ux * ux), Ry = sqrt(1.0 + 3.0 * uy * uy),
-               Rz = sqrt(1.0 + 3.0 * uz * uz);
-  const double ex = 3.0 * ux * ux / (1.0 + Rx), ey = 3.0 * uy * uy / (1.0 + Ry),
-               ez = 3.0 * uz * uz / (1.0 + Rz);
-  const double gx[3] = {drho + (2.0 * ex - 3.0 * ux) * rho, drho - ex * rho,
-                        drho + (2.0 * ex + 3.0 * ux) * rho};
-  const double fy[3] = {2.0 * ey - 3.0 * uy, -ey, 2.0 * ey + 3.0 * uy};
-  const double fz[3] = {2.0 * ez - 3.0 * uz, -ez, 2.0 * ez + 3.0 * uz};
+// Equilibrium shift f_eq_i(rho, u) - W_i by the same per-axis closed form, in the precision T
+// of the arguments (FP64 for initialisation, the collision precision for the pre-solve).
+template <typename T>
+__device__ __forceinline__ void equilibrium_shift(T rho, T ux, T uy, T uz, T (&out)[27]) {
+  const T one = T(1), two = T(2), three = T(3);
+  const T drho = rho - one;
+  const T Rx = sqrt(one + three * ux * ux), Ry = sqrt(one + three * uy * uy),
+          Rz = sqrt(one + three * uz * uz);
+  const T ex = three * ux * ux / (one + Rx), ey = three * uy * uy / (one + Ry),
+          ez = three * uz * uz / (one + Rz);
+  const T gx[3] = {drho + (two * ex - three * ux) * rho, drho - ex * rho,
+                   drho + (two * ex + three * ux) * rho};
+  const T fy[3] = {two * ey - three * uy, -ey, two * ey + three * uy};
+  const T fz[3] = {two * ez - three * uz, -ez, two * ez + three * uz};
 #pragma unroll
   for (int i = 0; i < 27; ++i) {
-    const double gxa = gx[cx(i) + 1], fyb = fy[cy(i) + 1], fzc = fz[cz(i) + 1];
-    const double P = gxa + fyb + gxa * fyb;
-    out[i] = wgt(i) * (P + fzc + P * fzc);
+    const T gxa = gx[cx(i) + 1], fyb = fy[cy(i) + 1], fzc = fz[cz(i) + 1];
+    const T P = gxa + fyb + gxa * fyb;
+    out[i] = T(wgt(i)) * (P + fzc + P * fzc);
   }
 }
 
@@ -586,7 +668,7 @@ template <int N> struct Unroll<N, N> {
 // ------------------------------------------------------------------ the fused node update
 // Loads f(x, t) of node (x, y, z) by the pattern of MODE, collides, stores f'(x) where
 // f(t+1) expects it. src and dst are the same buffer in the AA modes.
-template <typename S, int MODE, bool RECORD, bool CENTRAL = false>
+template <typename S, int MODE, bool RECORD, bool CENTRAL = false, bool EXACT = false>
 __device__ __forceinline__ void node_update(const S* src, S* dst, const Geo& g, uint32_t x,
                                             uint32_t y, uint32_t z, const CollideParams& cp,
                                             float* gamma_out, StepCounters* ctr) {
@@ -606,7 +688,7 @@ __device__ __forceinline__ void node_update(const S* src, S* dst, const Geo& g, 
     }
   });
   int guarded;
-  const R gamma = collide<R, CENTRAL>(d, cp, &guarded);
+  const R gamma = collide<R, CENTRAL, EXACT>(d, cp, &guarded);
   Unroll<0, 27>::run([&](auto ic) {
     constexpr int I = decltype(ic)::value;
     S* p = dst + (uint64_t)Pat::store_plane(I) * g.P + nb.template at<I, Pat::store_shift>();

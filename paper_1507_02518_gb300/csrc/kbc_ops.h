@@ -77,8 +77,22 @@ template <typename S> struct Ops {
   static cudaError_t moments(const BoxView& b, int64_t t, double* rho, double* u, uint64_t n0,
                              uint64_t cnt, uint64_t ld, cudaStream_t st);
   // diagnostics: writes u (arithmetic type of S) to ufield[3][P] and per-block partial sums
-  static cudaError_t diag(const BoxView& b, int64_t t, bool with_gamma, void* ufield,
+  // order: 2 or 8, the order of the central differences of the velocity gradients
+  static cudaError_t diag(const BoxView& b, int64_t t, bool with_gamma, int order, void* ufield,
                           double* partials, int nblocks, double* sums, cudaStream_t st);
+  // one density pre-solve iteration t -> t+1 with the velocity held at u0 ([3][P], collision
+  // precision); `store` keeps rho - 1 of f(t) in b.gamma for rho_change
+  static cudaError_t presolve_step(const BoxView& b, int64_t t, double beta_pre, const void* u0,
+                                   bool store, const StepOpts& o, cudaStream_t st);
+  // *resid = FP32 bits of max |rho(f(t)) - 1 - b.gamma| (zeroed first)
+  static cudaError_t rho_change(const BoxView& b, int64_t t, unsigned int* resid, int nblocks,
+                                cudaStream_t st);
+  // ufield[a][n0 + k] = u[a * ld + k] in the collision precision
+  static cudaError_t convert_u(const double* u, void* ufield, uint64_t n0, uint64_t cnt,
+                               uint64_t ld, uint64_t P, cudaStream_t st);
+  // stabilizer gap of canonical f(t): sums[0..6] as laid out by gap_kernel
+  static cudaError_t gamma_gap(const BoxView& b, int64_t t, double* partials, int nblocks,
+                               double* sums, cudaStream_t st);
   // one time step of every box of a batch over a work list
   // (packed: the FP32x2 two-nodes-per-thread form, 128 threads; FP32 arithmetic only)
   static cudaError_t batch_step(const BoxDesc* boxes, const WorkItem* items, int nitems,
@@ -89,7 +103,14 @@ template <typename S> struct Ops {
   static int batch_occupancy(int threads, int scheme, bool packed);
 };
 
-constexpr int kDiagSums = 16;   // layout of the diagnostics sums, see kbc_kernels.cuh
+// kinetic-energy spectrum (kbc_spectrum.cu): work bytes for an n^3 velocity field in FP64 or
+// FP32 with nbins shells (0 if cuFFT cannot plan it), and the spectrum itself; returns 0, or
+// 2 (work too small) / 3 (cuFFT or CUDA failure) with *why set
+size_t spectrum_work_bytes(uint32_t n, bool fp64, int nbins);
+int spectrum(const void* ufield, uint32_t n, bool fp64, int nbins, void* work, size_t work_bytes,
+             double* bins_host, cudaStream_t st, const char** why);
+
+constexpr int kDiagSums = 24;   // layout of the diagnostics sums, see kbc_kernels.cuh
 constexpr int kDiagBlocks = 608;  // fixed grid of the reduction kernels (4 per SM on 152 SMs)
 
 }  // namespace kbc

@@ -21,6 +21,7 @@ thread_local std::string g_create_error;
 
 constexpr size_t kAlign = 256;
 constexpr uint64_t kStageNodes = 1ull << 20;  // host-transfer chunk (nodes)
+constexpr int32_t kMaxSpectrumBins = 6144;     // shared-memory histogram of 48 KB
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
@@ -51,8 +52,8 @@ bool valid_config(const lb_config* c, std::string* why) {
     *why = "variant must be LB_S_D..LB_S_DTQ or LB_S_CD..LB_S_CDTQ";
     return false;
   }
-  if (c->gamma_mode < LB_GAMMA_ESTIMATE || c->gamma_mode > LB_GAMMA_RLB) {
-    *why = "gamma_mode must be LB_GAMMA_ESTIMATE, LB_GAMMA_LBGK or LB_GAMMA_RLB";
+  if (c->gamma_mode < LB_GAMMA_ESTIMATE || c->gamma_mode > LB_GAMMA_EXACT) {
+    *why = "gamma_mode must be LB_GAMMA_ESTIMATE, LB_GAMMA_LBGK, LB_GAMMA_RLB or LB_GAMMA_EXACT";
     return false;
   }
   if (c->storage < LB_F64 || c->storage > LB_F16) {
@@ -148,6 +149,7 @@ struct lb_ctx {
   int prefetch = 2;
   unsigned long long wait_budget = 2000000000ull;  // about 1 s at the SM clock
   int stall = 0;
+  int diag_order = 2;
   bool gamma_valid = false;
   bool batch_view = false;
   std::string err;
@@ -344,6 +346,92 @@ lb_status lb_init_field(lb_ctx* c, const double* rho, const double* u, int on_de
   return sync(c, "init");
 }
 
+lb_status lb_presolve(lb_ctx* c, const double* u0, int on_device, double nu_pre,
+                      int64_t max_iters, double tol, int64_t* iters, double* residual) {
+  if (!c) return LB_ERR_INVALID_ARG;
+  if (!u0) return fail(c, LB_ERR_INVALID_ARG, "u0 is NULL");
+  if (!(nu_pre > 0.0) || !std::isfinite(nu_pre))
+    return fail(c, LB_ERR_INVALID_ARG, "nu_pre must be finite and > 0");
+  if (max_iters < 0) return fail(c, LB_ERR_INVALID_ARG, "max_iters must be >= 0");
+  if (std::isnan(tol)) return fail(c, LB_ERR_INVALID_ARG, "tol is NaN");
+  const uint64_t P = c->box.P;
+  const double beta_pre = 1.0 / (6.0 * nu_pre + 1.0);
+  c->t = 0;
+  c->gamma_valid = false;
+  cudaError_t e = cudaSuccess;
+  // u0 into the diagnostics velocity field (collision precision), f = f_eq(1, u0) at t = 0
+  if (on_device) {
+    e = dispatch(c, [&](auto ops) { return ops.convert_u(u0, c->ufield, 0, P, P, P, c->stream); });
+    if (e == cudaSuccess)
+      e = dispatch(c, [&](auto ops) { return ops.init(c->box, 0, nullptr, u0, 0, P, P, c->stream); });
+    if (e != cudaSuccess) return cuda_fail(c, e, "pre-solve set-up");
+  } else {
+    for (uint64_t n0 = 0; n0 < P; n0 += c->stage_nodes) {
+      const uint64_t cnt = (P - n0 < c->stage_nodes) ? P - n0 : c->stage_nodes;
+      double* su = c->staging;
+      for (int a = 0; a < 3 && e == cudaSuccess; ++a)
+        e = cudaMemcpyAsync(su + a * cnt, u0 + a * P + n0, cnt * 8, cudaMemcpyHostToDevice,
+                            c->stream);
+      if (e == cudaSuccess)
+        e = dispatch(c, [&](auto ops) {
+          return ops.convert_u(su, c->ufield, n0, cnt, cnt, P, c->stream);
+        });
+      if (e == cudaSuccess)
+        e = dispatch(c, [&](auto ops) { return ops.init(c->box, 0, nullptr, su, n0, cnt, cnt, c->stream); });
+      if (e != cudaSuccess) return cuda_fail(c, e, "pre-solve set-up");
+    }
+  }
+  // iterations in chunks of kCheck; an even total keeps the state at an even time, where
+  // both schemes store it in the layout of t = 0
+  const int64_t kCheck = 32;
+  const int64_t total = max_iters + (max_iters & 1);
+  const kbc::StepOpts o = step_opts(c);
+  int64_t done = 0;
+  double res = NAN;
+  unsigned int* d_res = (unsigned int*)c->sums;
+  while (done < total) {
+    const int64_t chunk = (total - done < kCheck) ? total - done : kCheck;
+    for (int64_t j = 0; j < chunk && e == cudaSuccess; ++j) {
+      const bool store = (j == chunk - 1);
+      e = dispatch(c, [&](auto ops) {
+        return ops.presolve_step(c->box, c->t, beta_pre, c->ufield, store, o, c->stream);
+      });
+      c->t += 1;
+    }
+    if (e == cudaSuccess)
+      e = dispatch(c, [&](auto ops) {
+        return ops.rho_change(c->box, c->t, d_res, kbc::kDiagBlocks, c->stream);
+      });
+    unsigned int bits = 0;
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&bits, d_res, sizeof bits, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) {
+      c->t = 0;
+      return cuda_fail(c, e, "pre-solve iteration");
+    }
+    lb_status st = sync(c, "pre-solve");
+    if (st != LB_OK) {
+      c->t = 0;
+      return st;
+    }
+    float r;
+    memcpy(&r, &bits, sizeof r);
+    res = (double)r;
+    done += chunk;
+    if (std::isinf(res)) {
+      c->t = 0;
+      if (iters) *iters = done;
+      if (residual) *residual = res;
+      return fail(c, LB_ERR_NONFINITE, "the pre-solve produced NaN/Inf populations");
+    }
+    if (res <= tol) break;
+  }
+  c->t = 0;
+  if (iters) *iters = done;
+  if (residual) *residual = res;
+  return LB_OK;
+}
+
 lb_status lb_step(lb_ctx* c, int64_t n) {
   if (!c) return LB_ERR_INVALID_ARG;
   if (n < 0) return fail(c, LB_ERR_INVALID_ARG, "n must be >= 0");
@@ -391,7 +479,8 @@ lb_status lb_moments(lb_ctx* c, double* rho, double* u, int on_device) {
 lb_status lb_diagnostics(lb_ctx* c, lb_diag* out) {
   if (!c || !out) return c ? fail(c, LB_ERR_INVALID_ARG, "out is NULL") : LB_ERR_INVALID_ARG;
   cudaError_t e = dispatch(c, [&](auto ops) {
-    return ops.diag(c->box, c->t, c->gamma_valid, c->ufield, c->partials, kbc::kDiagBlocks,
+    return ops.diag(c->box, c->t, c->gamma_valid, c->diag_order, c->ufield, c->partials,
+                    kbc::kDiagBlocks,
                     c->sums, c->stream);
   });
   if (e != cudaSuccess) return cuda_fail(c, e, "diagnostics kernels");
@@ -423,6 +512,12 @@ lb_status lb_diagnostics(lb_ctx* c, lb_diag* out) {
     out->gamma_std = NAN;
     out->den_guard_count = 0;
   }
+  out->grad_order = c->diag_order;
+  out->reserved = 0;
+  const double m2 = s[13] / P;
+  out->dudx2 = m2;
+  for (int m = 3; m <= 6; ++m)
+    out->skewness[m - 3] = (m % 2 ? -1.0 : 1.0) * (s[13 + m - 2] / P) / std::pow(m2, 0.5 * m);
   out->nonfinite_count = (int64_t)s[10];
   if (out->nonfinite_count > 0) {
     char buf[96];
@@ -430,6 +525,75 @@ lb_status lb_diagnostics(lb_ctx* c, lb_diag* out) {
              (long long)out->nonfinite_count, (long long)c->t);
     return fail(c, LB_ERR_NONFINITE, buf);
   }
+  return LB_OK;
+}
+
+static bool spectrum_args(lb_ctx* c, int32_t nbins, lb_status* st) {
+  if (c->box.nx != c->box.ny || c->box.nx != c->box.nz) {
+    *st = fail(c, LB_ERR_UNSUPPORTED, "the spectrum is defined on cubic boxes only");
+    return false;
+  }
+  if (nbins < 1 || nbins > kMaxSpectrumBins) {
+    *st = fail(c, LB_ERR_INVALID_ARG, "nbins must be in 1..6144");
+    return false;
+  }
+  return true;
+}
+
+size_t lb_spectrum_work_bytes(lb_ctx* c, int32_t nbins) {
+  lb_status st;
+  if (!c || !spectrum_args(c, nbins, &st)) return 0;
+  return kbc::spectrum_work_bytes(c->box.nx, c->cfg.storage == LB_F64, nbins);
+}
+
+lb_status lb_spectrum(lb_ctx* c, void* work, size_t work_bytes, int32_t nbins, double* E) {
+  if (!c) return LB_ERR_INVALID_ARG;
+  if (!work || !E) return fail(c, LB_ERR_INVALID_ARG, "work or E is NULL");
+  lb_status st;
+  if (!spectrum_args(c, nbins, &st)) return st;
+  if (((uintptr_t)work % kAlign) != 0)
+    return fail(c, LB_ERR_INVALID_ARG, "work must be 256-byte aligned");
+  // the velocity field of the current state, as lb_diagnostics computes it
+  cudaError_t e = dispatch(c, [&](auto ops) {
+    return ops.diag(c->box, c->t, c->gamma_valid, c->diag_order, c->ufield, c->partials,
+                    kbc::kDiagBlocks, c->sums, c->stream);
+  });
+  if (e != cudaSuccess) return cuda_fail(c, e, "velocity field");
+  const char* why = "";
+  const int r = kbc::spectrum(c->ufield, c->box.nx, c->cfg.storage == LB_F64, nbins, work,
+                              work_bytes, E, c->stream, &why);
+  if (r == 2) return fail(c, LB_ERR_INVALID_ARG, why);
+  if (r != 0) return fail(c, LB_ERR_CUDA, std::string("spectrum: ") + why);
+  return sync(c, "spectrum");
+}
+
+lb_status lb_set_diag_order(lb_ctx* c, int32_t order) {
+  if (!c) return LB_ERR_INVALID_ARG;
+  if (order != 2 && order != 8) return fail(c, LB_ERR_INVALID_ARG, "order must be 2 or 8");
+  c->diag_order = order;
+  return LB_OK;
+}
+
+lb_status lb_stabilizer_gap(lb_ctx* c, lb_gap* out) {
+  if (!c || !out) return c ? fail(c, LB_ERR_INVALID_ARG, "out is NULL") : LB_ERR_INVALID_ARG;
+  cudaError_t e = dispatch(c, [&](auto ops) {
+    return ops.gamma_gap(c->box, c->t, c->partials, kbc::kDiagBlocks, c->sums, c->stream);
+  });
+  if (e != cudaSuccess) return cuda_fail(c, e, "stabilizer gap kernels");
+  double s[7];
+  e = cudaMemcpyAsync(s, c->sums, sizeof s, cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "copying the stabilizer gap");
+  lb_status st = sync(c, "stabilizer gap");
+  if (st != LB_OK) return st;
+  const double n = s[0];
+  out->step = c->t;
+  out->nodes = (int64_t)n;
+  out->mean_abs = n > 0 ? s[1] / n : NAN;
+  out->max_abs = n > 0 ? s[6] : NAN;
+  out->mean_estimate = n > 0 ? s[2] / n : NAN;
+  out->mean_exact = n > 0 ? s[3] / n : NAN;
+  out->unconverged = (int64_t)s[4];
+  out->skipped = (int64_t)s[5];
   return LB_OK;
 }
 
@@ -498,6 +662,8 @@ lb_status lb_set_kernel(lb_ctx* c, int32_t kind) {
   if ((kind == LB_KERNEL_STAGED || kind == LB_KERNEL_PERSISTENT) && c->box.central)
     return fail(c, LB_ERR_UNSUPPORTED, "the staged and persistent kernels implement the natural-"
                                        "moment variants only");
+  if (c->cfg.gamma_mode == LB_GAMMA_EXACT && kind != LB_KERNEL_AUTO && kind != LB_KERNEL_DIRECT)
+    return fail(c, LB_ERR_UNSUPPORTED, "the exact stabilizer runs in the direct kernel only");
   if (kind == LB_KERNEL_PACKED && c->cfg.storage == LB_F64)
     return fail(c, LB_ERR_UNSUPPORTED, "the packed FP32x2 kernel needs FP32 arithmetic "
                                        "(LB_F32 or LB_F16 storage)");
@@ -720,6 +886,10 @@ lb_status lb_batch_create(const lb_config* cfgs, int32_t nbox, void* dev_buf, si
   if (!batch_layout(cfgs, nbox, &L, &why)) {
     g_create_error = why;
     return LB_ERR_INVALID_ARG;
+  }
+  if (cfgs[0].gamma_mode == LB_GAMMA_EXACT) {
+    g_create_error = "the batch kernels do not implement the exact stabilizer";
+    return LB_ERR_UNSUPPORTED;
   }
   if (!dev_buf || ((uintptr_t)dev_buf % kAlign) != 0) {
     g_create_error = "dev_buf must be a non-NULL 256-byte aligned device pointer";

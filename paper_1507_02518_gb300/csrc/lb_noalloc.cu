@@ -256,6 +256,10 @@ lb_status lb_diagnostics_noalloc(int32_t nx, int32_t ny, int32_t nz, double nu, 
   out->gamma_std = NAN;
   out->nonfinite_count = (int64_t)h[10];
   out->den_guard_count = 0;
+  out->grad_order = 2;
+  out->reserved = 0;
+  out->dudx2 = NAN;  // the longitudinal-derivative moments are not computed here
+  for (int m = 0; m < 4; ++m) out->skewness[m] = NAN;
   if (out->nonfinite_count > 0) {
     kbc_set_thread_error("the population field holds NaN/Inf");
     return LB_ERR_NONFINITE;

@@ -8,6 +8,7 @@ or cannot be loaded, ``load()`` raises.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import threading
 
@@ -19,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libkbc.so")
 LB_OK, LB_ERR_INVALID_ARG, LB_ERR_OOM, LB_ERR_CUDA, LB_ERR_NONFINITE, LB_ERR_TIMEOUT, \
     LB_ERR_UNSUPPORTED = range(7)
 LB_S_D, LB_S_DT, LB_S_DQ, LB_S_DTQ, LB_S_CD, LB_S_CDT, LB_S_CDQ, LB_S_CDTQ = range(8)
-LB_GAMMA_ESTIMATE, LB_GAMMA_LBGK, LB_GAMMA_RLB = range(3)
+LB_GAMMA_ESTIMATE, LB_GAMMA_LBGK, LB_GAMMA_RLB, LB_GAMMA_EXACT = range(4)
 LB_F64, LB_F32, LB_F16 = range(3)
 LB_PULL, LB_AA = range(2)
 LB_KERNEL_AUTO, LB_KERNEL_DIRECT, LB_KERNEL_STAGED, LB_KERNEL_PERSISTENT, \
@@ -31,7 +32,8 @@ STORAGE = {"f64": LB_F64, "f32": LB_F32, "f16": LB_F16}
 SCHEME = {"pull": LB_PULL, "aa": LB_AA}
 VARIANT = {"d": LB_S_D, "d+t": LB_S_DT, "d+q": LB_S_DQ, "d+t+q": LB_S_DTQ,
            "cd": LB_S_CD, "cd+ct": LB_S_CDT, "cd+cq": LB_S_CDQ, "cd+ct+cq": LB_S_CDTQ}
-GAMMA = {"estimate": LB_GAMMA_ESTIMATE, "lbgk": LB_GAMMA_LBGK, "rlb": LB_GAMMA_RLB}
+GAMMA = {"estimate": LB_GAMMA_ESTIMATE, "lbgk": LB_GAMMA_LBGK, "rlb": LB_GAMMA_RLB,
+         "exact": LB_GAMMA_EXACT}
 BYTES_PER_VALUE = {LB_F64: 8, LB_F32: 4, LB_F16: 2}
 
 
@@ -47,7 +49,9 @@ class lb_diag(ctypes.Structure):
                 ("momentum", ctypes.c_double * 3), ("kinetic_energy", ctypes.c_double),
                 ("enstrophy", ctypes.c_double), ("dissipation", ctypes.c_double),
                 ("gamma_mean", ctypes.c_double), ("gamma_std", ctypes.c_double),
-                ("nonfinite_count", ctypes.c_int64), ("den_guard_count", ctypes.c_int64)]
+                ("nonfinite_count", ctypes.c_int64), ("den_guard_count", ctypes.c_int64),
+                ("grad_order", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("dudx2", ctypes.c_double), ("skewness", ctypes.c_double * 4)]
 
     def as_dict(self):
         return {"step": self.step, "nodes": self.nodes, "mass": self.mass,
@@ -55,7 +59,18 @@ class lb_diag(ctypes.Structure):
                 "enstrophy": self.enstrophy, "dissipation": self.dissipation,
                 "gamma_mean": self.gamma_mean, "gamma_std": self.gamma_std,
                 "nonfinite_count": self.nonfinite_count,
-                "den_guard_count": self.den_guard_count}
+                "den_guard_count": self.den_guard_count, "grad_order": self.grad_order,
+                "dudx2": self.dudx2, "skewness": list(self.skewness)}
+
+
+class lb_gap(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int64), ("nodes", ctypes.c_int64),
+                ("mean_abs", ctypes.c_double), ("max_abs", ctypes.c_double),
+                ("mean_estimate", ctypes.c_double), ("mean_exact", ctypes.c_double),
+                ("unconverged", ctypes.c_int64), ("skipped", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 _lib = None
@@ -69,7 +84,8 @@ SYMBOLS = ["lb_required_bytes", "lb_create", "lb_destroy", "lb_last_error", "lb_
            "lb_batch_required_bytes", "lb_batch_create", "lb_batch_destroy",
            "lb_batch_last_error", "lb_batch_box", "lb_batch_step", "lb_batch_diagnostics",
            "lb_batch_autotune", "lb_batch_set_tile", "lb_batch_set_kernel",
-           "lb_diagnostics_noalloc"]
+           "lb_diagnostics_noalloc", "lb_stabilizer_gap", "lb_presolve", "lb_set_diag_order",
+           "lb_spectrum_work_bytes", "lb_spectrum"]
 
 
 class LBError(RuntimeError):
@@ -147,6 +163,17 @@ def load(path: str = LIB_PATH):
         L.lb_batch_set_kernel.argtypes = [vp, i32]
         L.lb_diagnostics_noalloc.restype = i32
         L.lb_diagnostics_noalloc.argtypes = [i32, i32, i32, d, vp, vp, ctypes.POINTER(lb_diag)]
+        L.lb_spectrum_work_bytes.restype = ctypes.c_size_t
+        L.lb_spectrum_work_bytes.argtypes = [vp, i32]
+        L.lb_spectrum.restype = i32
+        L.lb_spectrum.argtypes = [vp, vp, ctypes.c_size_t, i32, vp]
+        L.lb_set_diag_order.restype = i32
+        L.lb_set_diag_order.argtypes = [vp, i32]
+        L.lb_presolve.restype = i32
+        L.lb_presolve.argtypes = [vp, vp, ctypes.c_int, d, i64, d, ctypes.POINTER(i64),
+                                  ctypes.POINTER(d)]
+        L.lb_stabilizer_gap.restype = i32
+        L.lb_stabilizer_gap.argtypes = [vp, ctypes.POINTER(lb_gap)]
         _lib = L
         return L
 
@@ -195,6 +222,29 @@ def lb_init_field(ctx, rho_ptr: int, u_ptr: int, on_device: bool):
                                 int(on_device)), ctx)
 
 
+def lb_spectrum_work_bytes(ctx, nbins: int) -> int:
+    return int(load().lb_spectrum_work_bytes(ctx, int(nbins)))
+
+
+def lb_spectrum(ctx, work_ptr: int, work_bytes: int, nbins: int) -> np.ndarray:
+    E = np.zeros(int(nbins))
+    _check(load().lb_spectrum(ctx, ctypes.c_void_p(work_ptr), int(work_bytes), int(nbins),
+                              E.ctypes.data), ctx)
+    return E
+
+
+def lb_set_diag_order(ctx, order: int):
+    _check(load().lb_set_diag_order(ctx, int(order)), ctx)
+
+
+def lb_presolve(ctx, u0_ptr: int, on_device: bool, nu_pre: float, max_iters: int, tol: float):
+    it, res = ctypes.c_int64(), ctypes.c_double()
+    _check(load().lb_presolve(ctx, ctypes.c_void_p(u0_ptr), int(on_device), float(nu_pre),
+                              int(max_iters), float(tol), ctypes.byref(it), ctypes.byref(res)),
+           ctx)
+    return it.value, res.value
+
+
 def lb_step(ctx, n: int):
     _check(load().lb_step(ctx, int(n)), ctx)
 
@@ -226,6 +276,12 @@ def lb_diagnostics_noalloc(nx: int, ny: int, nz: int, nu: float, f_dev_ptr: int,
     if s != LB_OK:
         raise LBError(s, lb_last_error(None))
     return d
+
+
+def lb_stabilizer_gap(ctx) -> lb_gap:
+    g = lb_gap()
+    _check(load().lb_stabilizer_gap(ctx, ctypes.byref(g)), ctx)
+    return g
 
 
 def lb_get_populations(ctx, f_ptr: int, on_device: bool):
@@ -375,6 +431,16 @@ class Lattice:
             r = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64)
             lb_init_field(self.ctx, 0 if r is None else r.ctypes.data, u.ctypes.data, False)
 
+    def presolve(self, u0, nu_pre=1.0 / 6.0, max_iters=20000, tol=1e-9):
+        """Consistent initial state for the velocity u0 ([3,nz,ny,nx], numpy or CUDA tensor):
+        see lb_presolve. Returns (iterations, last change of rho)."""
+        torch = _torch()
+        if isinstance(u0, torch.Tensor) and u0.is_cuda:
+            u0 = u0.to(torch.float64).contiguous()
+            return lb_presolve(self.ctx, u0.data_ptr(), True, nu_pre, max_iters, tol)
+        u0 = np.ascontiguousarray(u0, dtype=np.float64)
+        return lb_presolve(self.ctx, u0.ctypes.data, False, nu_pre, max_iters, tol)
+
     def step(self, n=1):
         lb_step(self.ctx, n)
 
@@ -386,6 +452,30 @@ class Lattice:
 
     def diagnostics(self, raise_nonfinite=True) -> dict:
         return lb_diagnostics(self.ctx, raise_nonfinite).as_dict()
+
+    def spectrum(self, nbins=None):
+        """Shell-summed kinetic-energy spectrum E[m] (kappa = 2 pi m / N) of the current state;
+        nbins defaults to every shell of the cube. Work space comes from torch's allocator."""
+        torch = _torch()
+        if nbins is None:
+            nbins = int(math.sqrt(3.0) * self.shape[0] / 2.0) + 2
+        need = lb_spectrum_work_bytes(self.ctx, nbins)
+        if need == 0:
+            cubic = self.shape[0] == self.shape[1] == self.shape[2]
+            raise LBError(LB_ERR_INVALID_ARG if cubic else LB_ERR_UNSUPPORTED,
+                          lb_last_error(self.ctx))
+        with torch.cuda.stream(self.stream):
+            work = torch.empty(need + 256, dtype=torch.uint8, device="cuda")
+            ptr = (work.data_ptr() + 255) // 256 * 256
+            return lb_spectrum(self.ctx, ptr, need, nbins)
+
+    def set_diag_order(self, order):
+        """Central-difference order (2 or 8) of the velocity gradients in diagnostics()."""
+        lb_set_diag_order(self.ctx, order)
+
+    def stabilizer_gap(self) -> dict:
+        """<|gamma_est - gamma*|>, max, means and solver counts on the current state."""
+        return lb_stabilizer_gap(self.ctx).as_dict()
 
     def get_populations(self) -> np.ndarray:
         f = np.empty((27,) + self.shape)

@@ -93,7 +93,7 @@ def random_spectrum(n: int, k0: float, urms: float, seed: int, dtype=np.float64)
     a[0] -= KX * kdota
     a[1] -= KY * kdota
     a[2] -= KZ * kdota
-    u = np.stack([np.fft.irfftn(a[c], s=(n, n, n)) for c in range(3)])
+    u = np.stack([np.fft.irfftn(a[c], s=(n, n, n), axes=(0, 1, 2)) for c in range(3)])
     rms = math.sqrt(float(np.mean(np.sum(u * u, axis=0))) / 3.0)
     u *= urms / rms
     return np.ones((n, n, n)), u.astype(dtype, copy=False)

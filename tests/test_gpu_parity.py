@@ -420,6 +420,30 @@ def test_moments_and_diagnostics_match_oracle(kbc, scheme):
     assert d["gamma_std"] == pytest.approx(float(np.std(g_ref)), rel=1e-4, abs=1e-7)
     assert d["den_guard_count"] == guarded
     assert d["nonfinite_count"] == 0
+    assert d["grad_order"] == 2
+    assert np.allclose(d["skewness"], dref["skewness"], rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("storage,rel", [("f64", 1e-10), ("f32", 2e-4)])
+@pytest.mark.parametrize("shape", [(16, 16, 16), (20, 9, 5), (3, 3, 3)])
+def test_eighth_order_diagnostics_match_oracle(kbc, storage, rel, shape):
+    """Table 2's gradient statistics (8th-order central differences) on ragged and tiny boxes
+    (the 9-point stencil wraps more than once around a 3-node period)."""
+    nx, ny, nz = shape
+    f0 = seeded_state(nx, ny, nz, noise=1e-3)
+    lat = lattice(shape, nu=1e-3, storage=storage, scheme="aa")
+    lat.set_populations(f0)
+    lat.step(3)
+    lat.set_diag_order(8)
+    d = lat.diagnostics()
+    r, u = oracle.macroscopic(lat.get_populations())
+    dref = oracle.diagnostics(r, u, 1e-3, order=8)
+    assert d["grad_order"] == 8
+    for key in ("kinetic_energy", "enstrophy", "dissipation", "dudx2"):
+        assert d[key] == pytest.approx(dref[key], rel=rel), key
+    assert np.allclose(d["skewness"], dref["skewness"], rtol=50 * rel, atol=50 * rel)
+    with pytest.raises(lb.LBError):
+        lat.set_diag_order(4)
 
 
 def test_rest_state_is_exact_and_guarded(kbc):

@@ -94,3 +94,54 @@ def test_mean_flow_is_removed_from_statistics():
     d1 = oracle.diagnostics(rho, u2, 1e-3)
     for key in ("kinetic_energy", "enstrophy", "dissipation"):
         assert d1[key] == pytest.approx(d0[key], rel=1e-12)
+
+
+def test_eighth_order_gradients_converge_at_eighth_order():
+    """Omega of a shear wave with 8th-order differences approaches the continuum U^2 kappa^2 / 4
+    with an error that falls by 2^8 when the grid is refined by 2 (Table 2's stencils)."""
+    U = 0.03
+    errs = []
+    for ny in (16, 32):
+        rho, u = wl.shear_wave(3, ny, 3, U)
+        d = oracle.diagnostics(rho, u, 1e-3, order=8)
+        kk = 2 * math.pi / ny
+        errs.append(abs(d["enstrophy"] / (U * U * kk * kk / 4) - 1))
+    assert errs[0] < 5e-6
+    assert errs[0] / errs[1] == pytest.approx(256.0, rel=0.05), errs
+    # second order: the same wave gives sin^2(kappa) instead of kappa^2 (closed form above)
+    d2 = oracle.diagnostics(*wl.shear_wave(3, 16, 3, U), 1e-3, order=2)
+    assert d2["enstrophy"] == pytest.approx(U * U * math.sin(2 * math.pi / 16) ** 2 / 4,
+                                            rel=1e-12)
+
+
+@pytest.mark.parametrize("order", [2, 8])
+def test_skewness_factors_of_a_longitudinal_wave(order):
+    """u_x = U sin(kappa x): du_x/dx = U K cos(kappa x) for any difference order, so
+    S3 = S5 = 0, S4 = <cos^4>/<cos^2>^2 = 3/2, S6 = <cos^6>/<cos^2>^3 = 5/2."""
+    n = 24
+    u = np.zeros((3, 4, 3, n))
+    u[0] = 0.02 * np.sin(2 * math.pi * np.arange(n) / n)
+    d = oracle.diagnostics(np.ones((4, 3, n)), u, 1e-3, order=order)
+    s3, s4, s5, s6 = d["skewness"]
+    assert abs(s3) < 1e-12 and abs(s5) < 1e-12
+    assert s4 == pytest.approx(1.5, rel=1e-12)
+    assert s6 == pytest.approx(2.5, rel=1e-12)
+
+
+def test_skewness_factors_of_a_two_mode_wave_match_the_continuum():
+    """u_x = U (sin th + sin(2 th)/2), th = kappa x: du_x/dx = U kappa (cos th + cos 2 th) in the
+    continuum. Its S_n by quadrature on a fine grid; the 8th-order stencil on 32 points
+    reproduces them to the stencil's error."""
+    n = 32
+    th = 2 * math.pi * np.arange(n) / n
+    u = np.zeros((3, 3, 3, n))
+    u[0] = 0.01 * (np.sin(th) + 0.5 * np.sin(2 * th))
+    d = oracle.diagnostics(np.ones((3, 3, n)), u, 1e-3, order=8)
+    fine = 2 * math.pi * np.arange(4096) / 4096
+    g = np.cos(fine) + np.cos(2 * fine)
+    m2 = np.mean(g ** 2)
+    for i, m in enumerate((3, 4, 5, 6)):
+        expect = (-1) ** m * np.mean(g ** m) / m2 ** (m / 2)
+        assert d["skewness"][i] == pytest.approx(expect, rel=1e-5, abs=1e-9), (m, expect)
+    # by hand: <g^2> = 1, <g^3> = 3 <cos^2 th cos 2th> = 3/4, so S3 = -3/4
+    assert d["skewness"][0] == pytest.approx(-0.75, rel=1e-5)

@@ -296,6 +296,42 @@ def test_gamma_estimate_tends_to_exact_root():
         assert 1.6 < r < 2.4, (gaps, ratios)
 
 
+@pytest.mark.parametrize("seed,eps,nu", [(21, 1e-2, 1e-3), (22, 5e-2, 1e-4), (23, 2e-1, 1e-2),
+                                         (24, 3e-2, 0.3)])
+def test_gamma_exact_is_the_entropy_critical_point(seed, eps, nu):
+    """gamma* of the oracle equals a bracketing root (Brent) of dS/dgamma written out in numpy.
+
+    S(gamma) = -sum f'_i ln(f'_i / W_i) with f' = f - beta (2 ds + gamma dh) (eq:S, eq:Egeneral);
+    dS/dgamma = beta sum dh_i ln(f'_i / W_i) + beta sum dh_i, and sum dh_i = 0. The oracle solves
+    eq:result1 (logarithms relative to f_eq) by Newton's method; the two conditions agree because
+    ln(f_eq_i / W_i) is linear in (1, v_i) and dh carries no mass or momentum.
+    """
+    from scipy.optimize import brentq
+    rng = np.random.default_rng(seed)
+    b = oracle.beta(nu)
+    u = rng.uniform(-0.08, 0.08, 3)
+    f = oracle.equilibrium(1.0 + rng.uniform(-0.02, 0.02), u) * (1 + eps * rng.uniform(-1, 1, 27))
+    feq, ds, dh = oracle.deltas(f)
+    _, g0, _ = oracle.collide(f, b)
+    gex = oracle.gamma_exact(feq, ds, dh, b, g0)
+    _, gmode, _ = oracle.collide(f, b, oracle.S_DTQ, oracle.GAMMA_EXACT)
+    assert gmode == gex
+
+    def dsdg(g):
+        fp = f - b * (2 * ds + g * dh)
+        return float(np.sum(dh * np.log(fp / W)))
+
+    lo, hi = gex - 0.25, gex + 0.25
+    while np.any(f - b * (2 * ds + lo * dh) <= 0):
+        lo = 0.5 * (lo + gex)
+    while np.any(f - b * (2 * ds + hi * dh) <= 0):
+        hi = 0.5 * (hi + gex)
+    assert dsdg(lo) > 0 > dsdg(hi)          # S rises, then falls: a maximum in between
+    root = brentq(dsdg, lo, hi, xtol=1e-15, rtol=4 * np.finfo(float).eps, maxiter=200)
+    assert abs(gex - root) <= 1e-11 * (1 + abs(root)), (gex, root, g0)
+    assert abs(float(np.sum(dh))) <= 1e-15
+
+
 # ------------------------------------------------------------------ streaming
 
 def test_streaming_is_periodic_permutation():
