@@ -69,6 +69,11 @@ enum { LB_F64 = 0, LB_F32 = 1, LB_F16 = 2 };
 /* Streaming: LB_PULL keeps two population arrays (gather, collide, write);
  * LB_AA keeps one array updated in place with alternating even/odd steps. */
 enum { LB_PULL = 0, LB_AA = 1 };
+/* Equilibrium of the collision: the product form eq:entropic_eq (the method), or the
+ * second-order polynomial eq:polynomial2 (the standard LB equilibrium, a comparison mode; not
+ * with LB_GAMMA_EXACT, the batch kernels or the staged/persistent kernels). Initialisation
+ * (lb_init_field, lb_presolve) always uses the product form. */
+enum { LB_EQ_PRODUCT = 0, LB_EQ_POLY2 = 1 };
 
 typedef struct {
   int32_t nx, ny, nz;   /* periodic box, each >= 3, nx*ny*nz < 2^31 */
@@ -77,6 +82,7 @@ typedef struct {
   int32_t gamma_mode;   /* LB_GAMMA_* */
   int32_t storage;      /* LB_F64 / LB_F32 / LB_F16 */
   int32_t scheme;       /* LB_PULL / LB_AA */
+  int32_t equilibrium;  /* LB_EQ_PRODUCT (0) / LB_EQ_POLY2 */
 } lb_config;
 
 /* Diagnostics of Sec. "Numerical Simulations" at the current time t. Averages <.> are over
@@ -190,7 +196,8 @@ lb_status lb_spectrum(lb_ctx *ctx, void *work, size_t work_bytes, int32_t nbins,
 
 /* Fill *out with the stabilizer gap of the current state (NaN averages when no node was
  * evaluated). Does not advance t or touch the populations; uses the diagnostics work area.
- * Synchronises. Arithmetic in the collision precision of the storage (FP64 for LB_F64). */
+ * Synchronises. Arithmetic in the collision precision of the storage (FP64 for LB_F64).
+ * LB_ERR_UNSUPPORTED for LB_EQ_POLY2 contexts. */
 lb_status lb_stabilizer_gap(lb_ctx *ctx, lb_gap *out);
 
 /* Canonical pre-collision populations f[27][P] (FP64, caller-owned) at the current time t,

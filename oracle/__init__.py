@@ -34,6 +34,7 @@ _lib = None
 S_D, S_DT, S_DQ, S_DTQ = 0, 1, 2, 3
 S_CD, S_CDT, S_CDQ, S_CDTQ = 4, 5, 6, 7      # the same groups in the central-moment basis
 GAMMA_ESTIMATE, GAMMA_LBGK, GAMMA_RLB, GAMMA_EXACT = 0, 1, 2, 3
+EQ_POLY2 = 16          # OR'ed into a variant: the polynomial equilibrium eq:polynomial2
 DEN_GUARD = 1e-300
 
 
@@ -64,6 +65,7 @@ def lib():
             L.orc_beta.argtypes = [d]
             L.orc_lattice.argtypes = [vp, vp]
             L.orc_equilibrium.argtypes = [d, vp, vp]
+            L.orc_equilibrium_poly2.argtypes = [d, vp, vp]
             L.orc_moments.argtypes = [vp, vp, vp]
             L.orc_table1.argtypes = [vp, d, vp, vp, vp, vp]
             L.orc_moment_rep.argtypes = [vp, d, vp]
@@ -124,6 +126,14 @@ def equilibrium(rho: float, u) -> np.ndarray:
     u = _f64(u)
     out = np.zeros(27)
     lib().orc_equilibrium(float(rho), _p(u), _p(out))
+    return out
+
+
+def equilibrium_poly2(rho: float, u) -> np.ndarray:
+    """The second-order polynomial equilibrium eq:polynomial2."""
+    u = _f64(u)
+    out = np.zeros(27)
+    lib().orc_equilibrium_poly2(float(rho), _p(u), _p(out))
     return out
 
 

@@ -80,6 +80,24 @@ void orc_equilibrium(double rho, const double *u, double *feq) {
   }
 }
 
+/* eq:polynomial2 with c_s^2 = 1/3 (eq:sound):
+ * rho W_i (1 + (u.v_i)/c_s^2 + ((u.v_i)^2 - c_s^2 u.u) / (2 c_s^4)) */
+void orc_equilibrium_poly2(double rho, const double *u, double *feq) {
+  const double cs2 = 1.0 / 3.0;
+  const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  for (int i = 0; i < 27; ++i) {
+    const double uv = u[0] * vcomp(i, 0) + u[1] * vcomp(i, 1) + u[2] * vcomp(i, 2);
+    feq[i] = rho * weight(i) * (1.0 + uv / cs2 + (uv * uv - cs2 * uu) / (2.0 * cs2 * cs2));
+  }
+}
+
+static void equilibrium_of(int variant, double rho, const double *u, double *feq) {
+  if (variant & ORC_EQ_POLY2)
+    orc_equilibrium_poly2(rho, u, feq);
+  else
+    orc_equilibrium(rho, u, feq);
+}
+
 /* eq:natmoments: rho M_pqr = sum_i f_i vix^p viy^q viz^r; M stored at [p*9 + q*3 + r] */
 void orc_moments(const double *f, double *rho, double *M) {
   double r = 0.0;
@@ -272,7 +290,7 @@ static void shear_part(const double *d, const double *t, const double *q, int va
 /* k and the s groups of a population vector in the basis the variant names */
 static void groups(const double *f, int variant, double *rho, double *u, double *k, double *d,
                    double *t, double *q) {
-  if (variant >= ORC_S_CD) {
+  if ((variant & 15) >= ORC_S_CD) {
     double Mc[27], h[27];
     orc_central_moments(f, rho, u, Mc);
     orc_central_parts(Mc, *rho, u, k, d, t, q, h);
@@ -292,7 +310,7 @@ void orc_deltas(const double *f, int variant, double *feq, double *ds, double *d
   double k[27], d[27], t[27], q[27], s[27];
   double keq[27], deq[27], teq[27], qeq[27], seq[27];
   groups(f, variant, &rho, u, k, d, t, q);           /* step 1: rho, u; step 3: s */
-  orc_equilibrium(rho, u, feq);                      /* step 2 */
+  equilibrium_of(variant, rho, u, feq);              /* step 2 */
   groups(feq, variant, &rho_eq, u_eq, keq, deq, teq, qeq);  /* s_eq from the moments of f_eq */
   shear_part(d, t, q, variant, s);
   shear_part(deq, teq, qeq, variant, seq);
@@ -339,7 +357,7 @@ void orc_collide_mirror(const double *f, double beta, int variant, double gamma,
   double rho, u[3], feq[27], rho_eq, u_eq[3];
   double k[27], d[27], t[27], q[27], s[27], keq[27], deq[27], teq[27], qeq[27], seq[27];
   groups(f, variant, &rho, u, k, d, t, q);
-  orc_equilibrium(rho, u, feq);
+  equilibrium_of(variant, rho, u, feq);
   groups(feq, variant, &rho_eq, u_eq, keq, deq, teq, qeq);
   shear_part(d, t, q, variant, s);
   shear_part(deq, teq, qeq, variant, seq);

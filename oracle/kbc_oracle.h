@@ -28,6 +28,10 @@ enum {
   ORC_S_D = 0, ORC_S_DT = 1, ORC_S_DQ = 2, ORC_S_DTQ = 3,
   ORC_S_CD = 4, ORC_S_CDT = 5, ORC_S_CDQ = 6, ORC_S_CDTQ = 7
 };
+/* OR'ed into a variant argument: collide with the second-order polynomial equilibrium
+ * eq:polynomial2 instead of the product form eq:entropic_eq */
+#define ORC_EQ_POLY2 16
+
 /* how the stabilizer gamma is chosen */
 enum {
   ORC_GAMMA_ESTIMATE = 0, /* eq:result21 (the method) */
@@ -42,6 +46,7 @@ enum {
 void   orc_lattice(int32_t *v /*27x3*/, double *w /*27*/);
 double orc_beta(double nu);
 void   orc_equilibrium(double rho, const double *u /*3*/, double *feq /*27*/);
+void   orc_equilibrium_poly2(double rho, const double *u /*3*/, double *feq /*27*/);
 void   orc_moments(const double *f /*27*/, double *rho, double *M /*27: M[p*9+q*3+r]*/);
 void   orc_table1(const double *M, double rho, double *k, double *d, double *t, double *q);
 void   orc_moment_rep(const double *M, double rho, double *f /*27*/);

@@ -289,12 +289,15 @@ __device__ __noinline__ T newton_gamma(const T (&dh)[27], const T (&av)[27], con
 // bit k of *guarded is set when lane k's <dh|dh> fell under the guard.
 // EXACT (one node per thread only): gamma is the root of eq:result1 found by newton_gamma()
 // from the estimate; *gamma_est receives the estimate and *newton the solver's status.
-template <typename R, bool CENTRAL = false, bool EXACT = false>
+// POLY: the equilibrium is the second-order polynomial eq:polynomial2 instead of the product
+// form eq:entropic_eq (its moments, the populations for dh, and the entropic weights).
+template <typename R, bool CENTRAL = false, bool EXACT = false, bool POLY = false>
 __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, int* guarded,
                                      typename Ar<R>::Scalar* gamma_est = nullptr,
                                      int* newton = nullptr) {
   using O = Ar<R>;
   using T = typename O::Scalar;
+  static_assert(!(EXACT && POLY), "the exact stabilizer is built for the product form only");
   // ---- natural moments of delta by a factorised x -> y -> z reduction (eq:natmoments)
   // row r = (vy+1) + 3(vz+1); X0 = sum over vx, X1 = sum vx, X2 = sum vx^2
   R X0[9], X1[9], X2[9];
@@ -344,11 +347,26 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, int* g
     const R Rr = O::sqrt_fast(O::add(one, u3));
     return O::div_fast(u3, O::add(one, Rr));
   };
-  const R ex = axis_e(ux), ey = axis_e(uy), ez = axis_e(uz);
   const R c23 = O::c(2.0 / 3.0), c13 = O::c(1.0 / 3.0);
-  const R m2x = O::fma(c23, ex, c13);  // m_2(u) = (2R - 1)/3
-  const R m2y = O::fma(c23, ey, c13);
-  const R m2z = O::fma(c23, ez, c13);
+  // product form: e = R - 1 and the per-axis second moment m_2(u) = (2R - 1)/3 = 1/3 + 2e/3,
+  // which also scales the third moments (rho M_eq,120 = rho u_x m_2(u_y)).
+  // eq:polynomial2: e = 3u^2/2 gives the second moment 1/3 + u^2; its third moments are
+  // rho u_a / 3 (a, b, b) and 0 (x, y, z), so m3 = 1/3 there.
+  R ex, ey, ez, m3x, m3y, m3z;
+  if constexpr (POLY) {
+    const R c32 = O::c(1.5);
+    ex = O::mul(c32, O::mul(ux, ux));
+    ey = O::mul(c32, O::mul(uy, uy));
+    ez = O::mul(c32, O::mul(uz, uz));
+    m3x = m3y = m3z = c13;
+  } else {
+    ex = axis_e(ux);
+    ey = axis_e(uy);
+    ez = axis_e(uz);
+    m3x = O::fma(c23, ex, c13);
+    m3y = O::fma(c23, ey, c13);
+    m3z = O::fma(c23, ez, c13);
+  }
 
   // ---- rho-scaled moment deviations rho (M - M_eq) (listing steps 3-4)
   const R nrc23 = O::neg(O::mul(rho, c23));
@@ -364,10 +382,10 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, int* g
   const R APyz = O::fma(nD010, uz, D011);
   const R qs = O::c(cp.with_q ? 1.0 : 0.0);
   // third-order natural deviations rho (M - M_eq), before the variant mask
-  const R RQxyy = O::fma(nD100, m2y, D120), RQxzz = O::fma(nD100, m2z, D102);
-  const R RQxxy = O::fma(nD010, m2x, D210), RQyzz = O::fma(nD010, m2z, D012);
-  const R RQxxz = O::fma(nD001, m2x, D201), RQyyz = O::fma(nD001, m2y, D021);
-  const R RQxyz = O::fma(O::neg(O::mul(D100, uy)), uz, D111);
+  const R RQxyy = O::fma(nD100, m3y, D120), RQxzz = O::fma(nD100, m3z, D102);
+  const R RQxxy = O::fma(nD010, m3x, D210), RQyzz = O::fma(nD010, m3z, D012);
+  const R RQxxz = O::fma(nD001, m3x, D201), RQyyz = O::fma(nD001, m3y, D021);
+  const R RQxyz = POLY ? D111 : O::fma(O::neg(O::mul(D100, uy)), uz, D111);
   const R AQxyy = O::mul(qs, RQxyy), AQxzz = O::mul(qs, RQxzz);
   const R AQxxy = O::mul(qs, RQxxy), AQyzz = O::mul(qs, RQyzz);
   const R AQxxz = O::mul(qs, RQxxz), AQyyz = O::mul(qs, RQyyz);
@@ -411,28 +429,41 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, int* g
 
   // equilibrium factors: rho phi_x(a) = W_a (1 + gx_a), phi_y(b) = W_b (1 + fy_b), ...
   // with e_0 = -e, e_{+-1} = 2e +- 3u; the x factor carries rho: gx = drho + rho e_x
-  const R tex = O::add(ex, ex), tey = O::add(ey, ey), tez = O::add(ez, ez);
-  const R ux3 = O::mul(three, ux), uy3 = O::mul(three, uy), uz3 = O::mul(three, uz);
-  const R gx[3] = {O::fma(rho, O::sub(tex, ux3), drho), O::fma(O::neg(rho), ex, drho),
-                   O::fma(rho, O::add(tex, ux3), drho)};
-  const R fy[3] = {O::sub(tey, uy3), O::neg(ey), O::add(tey, uy3)};
-  const R fz[3] = {O::sub(tez, uz3), O::neg(ez), O::add(tez, uz3)};
+  // (product form only; eq:polynomial2 is evaluated per direction in the loop below)
+  R gx[3], fy[3], fz[3];
   // reciprocal weights of the entropic scalar product, 1/f_eq_i = rx[a] ry[b] rz[c]
-  auto recip_axis = [&](const R (&e)[3], R (&r)[3]) {
-    const R p0 = O::mul(c16, O::add(one, e[0]));
-    const R p1 = O::mul(c23, O::add(one, e[1]));
-    const R p2 = O::mul(c16, O::add(one, e[2]));
-    const R p12 = O::mul(p1, p2);
-    const R q = O::div_fast(one, O::mul(p0, p12));   // one division for three reciprocals
-    const R qp0 = O::mul(q, p0);
-    r[0] = O::mul(p12, q);
-    r[1] = O::mul(p2, qp0);
-    r[2] = O::mul(p1, qp0);
-  };
   R rx[3], ry[3], rz[3];
-  recip_axis(gx, rx);
-  recip_axis(fy, ry);
-  recip_axis(fz, rz);
+  if constexpr (!POLY) {
+    const R tex = O::add(ex, ex), tey = O::add(ey, ey), tez = O::add(ez, ez);
+    const R ux3 = O::mul(three, ux), uy3 = O::mul(three, uy), uz3 = O::mul(three, uz);
+    gx[0] = O::fma(rho, O::sub(tex, ux3), drho);
+    gx[1] = O::fma(O::neg(rho), ex, drho);
+    gx[2] = O::fma(rho, O::add(tex, ux3), drho);
+    fy[0] = O::sub(tey, uy3);
+    fy[1] = O::neg(ey);
+    fy[2] = O::add(tey, uy3);
+    fz[0] = O::sub(tez, uz3);
+    fz[1] = O::neg(ez);
+    fz[2] = O::add(tez, uz3);
+    auto recip_axis = [&](const R (&e)[3], R (&r)[3]) {
+      const R p0 = O::mul(c16, O::add(one, e[0]));
+      const R p1 = O::mul(c23, O::add(one, e[1]));
+      const R p2 = O::mul(c16, O::add(one, e[2]));
+      const R p12 = O::mul(p1, p2);
+      const R q = O::div_fast(one, O::mul(p0, p12));   // one division for three reciprocals
+      const R qp0 = O::mul(q, p0);
+      r[0] = O::mul(p12, q);
+      r[1] = O::mul(p2, qp0);
+      r[2] = O::mul(p1, qp0);
+    };
+    recip_axis(gx, rx);
+    recip_axis(fy, ry);
+    recip_axis(fz, rz);
+  }
+  // eq:polynomial2 with c_s^2 = 1/3: (f_eq_i - W_i)/W_i = drho + rho (3 s + 9/2 s^2 - 3/2 u.u),
+  // s = u.v_i
+  [[maybe_unused]] const R nu15 =
+      POLY ? O::mul(O::c(-1.5), O::fma(ux, ux, O::fma(uy, uy, O::mul(uz, uz)))) : O::c(0.0);
 
   // ---- dh, the two entropic products, and the part of the relaxation known before gamma
   // (listing steps 5-6): d <- d - 2 beta ds, dh kept for the gamma-dependent part
@@ -444,10 +475,12 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, int* g
   R num = O::c(0.0), den = O::c(0.0);
   // (1 + gx)(1 + fy) - 1 for the 9 (a, b) pairs, shared by the three z levels
   R Pab[9];
+  if constexpr (!POLY) {
 #pragma unroll
-  for (int b = 0; b < 3; ++b)
+    for (int b = 0; b < 3; ++b)
 #pragma unroll
-    for (int a = 0; a < 3; ++a) Pab[a + 3 * b] = O::fma(gx[a], fy[b], O::add(gx[a], fy[b]));
+      for (int a = 0; a < 3; ++a) Pab[a + 3 * b] = O::fma(gx[a], fy[b], O::add(gx[a], fy[b]));
+  }
   // Central-moment variants (appendix): the shear part is built on the central moments.
   // Their deviations follow from the natural ones because rho and u are conserved: second
   // order unchanged, third order rho dMc_120 = rho dM_120 - 2 uy rho dM_110 - ux rho dM_020
@@ -515,9 +548,20 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, int* g
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const int i = a + 3 * b + 9 * c;
-        // (f_eq_i - W_i)/W_i = (1 + gx)(1 + fy)(1 + fz) - 1 without cancellation
-        const R P = Pab[a + 3 * b];
-        const R G = O::fma(P, fz[c], O::add(P, fz[c]));
+        R G, wi;  // (f_eq_i - W_i)/W_i, and the x weight (product) or 1/f_eq_i (polynomial)
+        if constexpr (POLY) {
+          R sv = O::c(0.0);
+          if (a != 1) sv = a == 2 ? O::add(sv, ux) : O::sub(sv, ux);
+          if (b != 1) sv = b == 2 ? O::add(sv, uy) : O::sub(sv, uy);
+          if (c != 1) sv = c == 2 ? O::add(sv, uz) : O::sub(sv, uz);
+          G = O::fma(rho, O::fma(sv, O::fma(O::c(4.5), sv, three), nu15), drho);
+          wi = O::mul(O::c(inv_wgt(i)), O::div_fast(one, O::add(one, G)));
+        } else {
+          // (1 + gx)(1 + fy)(1 + fz) - 1 without cancellation
+          const R P = Pab[a + 3 * b];
+          G = O::fma(P, fz[c], O::add(P, fz[c]));
+          wi = rx[a];
+        }
         R dsi;
         if constexpr (CENTRAL) {
           const R* cx = cxv[a];
@@ -526,18 +570,28 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, int* g
           dsi = ds_of(a - 1, b - 1, c - 1);
         }
         const R dhi = O::sub(O::fma(O::c(-wgt(i)), G, d[i]), dsi);
-        const R t1 = O::mul(rx[a], dhi);
+        const R t1 = O::mul(wi, dhi);
         rn = O::fma(t1, dsi, rn);
         rd = O::fma(t1, dhi, rd);
         dh[i] = dhi;
         if constexpr (EXACT) av[i] = O::fma(nc2, dsi, dhi);
         d[i] = O::fma(nb2, dsi, d[i]);
       }
-      cn = O::fma(ry[b], rn, cn);
-      cd = O::fma(ry[b], rd, cd);
+      if constexpr (POLY) {
+        cn = O::add(rn, cn);
+        cd = O::add(rd, cd);
+      } else {
+        cn = O::fma(ry[b], rn, cn);
+        cd = O::fma(ry[b], rd, cd);
+      }
     }
-    num = O::fma(rz[c], cn, num);
-    den = O::fma(rz[c], cd, den);
+    if constexpr (POLY) {
+      num = O::add(cn, num);
+      den = O::add(cd, den);
+    } else {
+      num = O::fma(rz[c], cn, num);
+      den = O::fma(rz[c], cd, den);
+    }
   }
 
   // ---- stabilizer (eq:result21) and the rest of the relaxation (listing step 7)
@@ -668,7 +722,8 @@ template <int N> struct Unroll<N, N> {
 // ------------------------------------------------------------------ the fused node update
 // Loads f(x, t) of node (x, y, z) by the pattern of MODE, collides, stores f'(x) where
 // f(t+1) expects it. src and dst are the same buffer in the AA modes.
-template <typename S, int MODE, bool RECORD, bool CENTRAL = false, bool EXACT = false>
+template <typename S, int MODE, bool RECORD, bool CENTRAL = false, bool EXACT = false,
+          bool POLY = false>
 __device__ __forceinline__ void node_update(const S* src, S* dst, const Geo& g, uint32_t x,
                                             uint32_t y, uint32_t z, const CollideParams& cp,
                                             float* gamma_out, StepCounters* ctr) {
@@ -688,7 +743,7 @@ __device__ __forceinline__ void node_update(const S* src, S* dst, const Geo& g, 
     }
   });
   int guarded;
-  const R gamma = collide<R, CENTRAL, EXACT>(d, cp, &guarded);
+  const R gamma = collide<R, CENTRAL, EXACT, POLY>(d, cp, &guarded);
   Unroll<0, 27>::run([&](auto ic) {
     constexpr int I = decltype(ic)::value;
     S* p = dst + (uint64_t)Pat::store_plane(I) * g.P + nb.template at<I, Pat::store_shift>();
@@ -704,7 +759,7 @@ __device__ __forceinline__ void node_update(const S* src, S* dst, const Geo& g, 
 // of a warp stays coalesced; the collision runs once on float2 lanes with packed FP32x2
 // instructions. When xb is outside the box (vb false) lane 1 recomputes node xa and is not
 // stored. FP32 arithmetic only (S = float or uint16_t).
-template <typename S, int MODE, bool RECORD, bool CENTRAL = false>
+template <typename S, int MODE, bool RECORD, bool CENTRAL = false, bool POLY = false>
 __device__ __forceinline__ void node_update2(const S* src, S* dst, const Geo& g, uint32_t xa,
                                              uint32_t xb, bool vb, uint32_t y, uint32_t z,
                                              const CollideParams& cp, float* gamma_out,
@@ -723,10 +778,16 @@ __device__ __forceinline__ void node_update2(const S* src, S* dst, const Geo& g,
         base + na.template at<I, Pat::load_shift>(), base + nb.template at<I, Pat::load_shift>());
   });
   int guarded;
-  const float2 gamma = collide<float2, CENTRAL>(d, cp, &guarded);
+  const float2 gamma = collide<float2, CENTRAL, false, POLY>(d, cp, &guarded);
+  // In the AA modes the stores reuse the load addresses' planes; opaque copies of P and dst
+  // make the compiler recompute the store addresses instead of keeping 27 64-bit addresses
+  // live across the collision (which spilled at 3 blocks per SM).
+  uint64_t Ps = g.P;
+  S* dsts = dst;
+  if constexpr (MODE != MODE_PULL) asm volatile("" : "+l"(Ps), "+l"(dsts));
   Unroll<0, 27>::run([&](auto ic) {
     constexpr int I = decltype(ic)::value;
-    S* base = dst + (uint64_t)Pat::store_plane(I) * g.P;
+    S* base = dsts + (uint64_t)Pat::store_plane(I) * Ps;
     Codec2<S>::template store<I>(base + na.template at<I, Pat::store_shift>(),
                                  base + nb.template at<I, Pat::store_shift>(), vb, d[I]);
   });

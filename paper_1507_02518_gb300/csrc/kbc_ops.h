@@ -14,6 +14,7 @@ struct BoxView {
   double beta;
   int with_t, with_q, gamma_mode;
   int central;         // shear part in the central-moment basis
+  int poly;            // polynomial equilibrium eq:polynomial2 instead of the product form
   int scheme;          // 0 pull, 1 AA
 };
 

@@ -64,6 +64,10 @@ bool valid_config(const lb_config* c, std::string* why) {
     *why = "scheme must be LB_PULL or LB_AA";
     return false;
   }
+  if (c->equilibrium != LB_EQ_PRODUCT && c->equilibrium != LB_EQ_POLY2) {
+    *why = "equilibrium must be LB_EQ_PRODUCT or LB_EQ_POLY2";
+    return false;
+  }
   return true;
 }
 
@@ -188,6 +192,7 @@ void setup_ctx(lb_ctx* c, const lb_config* cfg, char* base, const BoxLayout& B,
   c->box.with_t = (v == LB_S_DT || v == LB_S_DTQ);
   c->box.with_q = (v == LB_S_DQ || v == LB_S_DTQ);
   c->box.central = cfg->variant >= LB_S_CD;
+  c->box.poly = cfg->equilibrium == LB_EQ_POLY2;
   c->box.gamma_mode = cfg->gamma_mode;
   c->box.scheme = cfg->scheme;
   c->counters = (kbc::StepCounters*)(base + B.counters);
@@ -273,6 +278,10 @@ lb_status lb_create(const lb_config* cfg, void* dev_buf, size_t bytes, void* str
   if (!valid_config(cfg, &why)) {
     g_create_error = why;
     return LB_ERR_INVALID_ARG;
+  }
+  if (cfg->equilibrium == LB_EQ_POLY2 && cfg->gamma_mode == LB_GAMMA_EXACT) {
+    g_create_error = "the exact stabilizer is built for the product-form equilibrium only";
+    return LB_ERR_UNSUPPORTED;
   }
   if (!dev_buf || ((uintptr_t)dev_buf % kAlign) != 0) {
     g_create_error = "dev_buf must be a non-NULL 256-byte aligned device pointer";
@@ -495,7 +504,7 @@ lb_status lb_diagnostics(lb_ctx* c, lb_diag* out) {
   const double P = (double)c->box.P;
   out->step = c->t;
   out->nodes = (int64_t)c->box.P;
-  out->mass = s[0];
+  out->mass = (P - s[10]) + s[0];  // finite nodes: their count plus the sum of rho - 1
   for (int a = 0; a < 3; ++a) out->momentum[a] = s[1 + a];
   const double mx = s[4] / P, my = s[5] / P, mz = s[6] / P;
   out->kinetic_energy = 0.5 * (s[7] / P - (mx * mx + my * my + mz * mz));
@@ -576,6 +585,9 @@ lb_status lb_set_diag_order(lb_ctx* c, int32_t order) {
 
 lb_status lb_stabilizer_gap(lb_ctx* c, lb_gap* out) {
   if (!c || !out) return c ? fail(c, LB_ERR_INVALID_ARG, "out is NULL") : LB_ERR_INVALID_ARG;
+  if (c->box.poly)
+    return fail(c, LB_ERR_UNSUPPORTED, "the stabilizer gap is built for the product-form "
+                                       "equilibrium only");
   cudaError_t e = dispatch(c, [&](auto ops) {
     return ops.gamma_gap(c->box, c->t, c->partials, kbc::kDiagBlocks, c->sums, c->stream);
   });
@@ -659,6 +671,9 @@ lb_status lb_set_kernel(lb_ctx* c, int32_t kind) {
   if (kind < LB_KERNEL_AUTO || kind > LB_KERNEL_PACKED)
     return fail(c, LB_ERR_INVALID_ARG, "kind must be LB_KERNEL_AUTO, _DIRECT, _STAGED, "
                                        "_PERSISTENT or _PACKED");
+  if ((kind == LB_KERNEL_STAGED || kind == LB_KERNEL_PERSISTENT) && c->box.poly)
+    return fail(c, LB_ERR_UNSUPPORTED, "the staged and persistent kernels implement the "
+                                       "product-form equilibrium only");
   if ((kind == LB_KERNEL_STAGED || kind == LB_KERNEL_PERSISTENT) && c->box.central)
     return fail(c, LB_ERR_UNSUPPORTED, "the staged and persistent kernels implement the natural-"
                                        "moment variants only");
@@ -760,6 +775,7 @@ bool batch_layout(const lb_config* cfgs, int32_t nbox, BatchLayout* L, std::stri
     c.gamma_mode = cfgs[0].gamma_mode;
     c.storage = cfgs[0].storage;
     c.scheme = cfgs[0].scheme;
+    c.equilibrium = cfgs[0].equilibrium;
     if (!valid_config(&c, why)) {
       *why = "box " + std::to_string(b) + ": " + *why;
       return false;
@@ -779,6 +795,7 @@ bool batch_layout(const lb_config* cfgs, int32_t nbox, BatchLayout* L, std::stri
     lb_config c = cfgs[b];
     c.storage = cfgs[0].storage;
     c.scheme = cfgs[0].scheme;
+    c.equilibrium = cfgs[0].equilibrium;
     BoxLayout B = box_layout(&c, off);
     L->box.push_back(B);
     off = B.total;
@@ -891,6 +908,10 @@ lb_status lb_batch_create(const lb_config* cfgs, int32_t nbox, void* dev_buf, si
     g_create_error = "the batch kernels do not implement the exact stabilizer";
     return LB_ERR_UNSUPPORTED;
   }
+  if (cfgs[0].equilibrium == LB_EQ_POLY2) {
+    g_create_error = "the batch kernels implement the product-form equilibrium only";
+    return LB_ERR_UNSUPPORTED;
+  }
   if (!dev_buf || ((uintptr_t)dev_buf % kAlign) != 0) {
     g_create_error = "dev_buf must be a non-NULL 256-byte aligned device pointer";
     return LB_ERR_INVALID_ARG;
@@ -930,6 +951,7 @@ lb_status lb_batch_create(const lb_config* cfgs, int32_t nbox, void* dev_buf, si
     c.gamma_mode = cfgs[0].gamma_mode;
     c.storage = cfgs[0].storage;
     c.scheme = cfgs[0].scheme;
+    c.equilibrium = cfgs[0].equilibrium;
     b->cfgs.push_back(c);
     lb_ctx* v = new lb_ctx();
     setup_ctx(v, &c, base, L.box[k], L.shared, b->stream);

@@ -23,6 +23,7 @@ LB_S_D, LB_S_DT, LB_S_DQ, LB_S_DTQ, LB_S_CD, LB_S_CDT, LB_S_CDQ, LB_S_CDTQ = ran
 LB_GAMMA_ESTIMATE, LB_GAMMA_LBGK, LB_GAMMA_RLB, LB_GAMMA_EXACT = range(4)
 LB_F64, LB_F32, LB_F16 = range(3)
 LB_PULL, LB_AA = range(2)
+LB_EQ_PRODUCT, LB_EQ_POLY2 = range(2)
 LB_KERNEL_AUTO, LB_KERNEL_DIRECT, LB_KERNEL_STAGED, LB_KERNEL_PERSISTENT, \
     LB_KERNEL_PACKED = range(5)
 KERNEL = {"auto": LB_KERNEL_AUTO, "direct": LB_KERNEL_DIRECT, "staged": LB_KERNEL_STAGED,
@@ -34,6 +35,7 @@ VARIANT = {"d": LB_S_D, "d+t": LB_S_DT, "d+q": LB_S_DQ, "d+t+q": LB_S_DTQ,
            "cd": LB_S_CD, "cd+ct": LB_S_CDT, "cd+cq": LB_S_CDQ, "cd+ct+cq": LB_S_CDTQ}
 GAMMA = {"estimate": LB_GAMMA_ESTIMATE, "lbgk": LB_GAMMA_LBGK, "rlb": LB_GAMMA_RLB,
          "exact": LB_GAMMA_EXACT}
+EQUILIBRIUM = {"product": LB_EQ_PRODUCT, "poly2": LB_EQ_POLY2}
 BYTES_PER_VALUE = {LB_F64: 8, LB_F32: 4, LB_F16: 2}
 
 
@@ -41,7 +43,7 @@ class lb_config(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("nu", ctypes.c_double), ("variant", ctypes.c_int32),
                 ("gamma_mode", ctypes.c_int32), ("storage", ctypes.c_int32),
-                ("scheme", ctypes.c_int32)]
+                ("scheme", ctypes.c_int32), ("equilibrium", ctypes.c_int32)]
 
 
 class lb_diag(ctypes.Structure):
@@ -186,14 +188,15 @@ def _check(status, ctx=None, batch=False):
 
 
 def make_config(nx, ny=None, nz=None, nu=1e-3, variant="d+t+q", gamma="estimate", storage="f32",
-                scheme="pull") -> lb_config:
+                scheme="pull", equilibrium="product") -> lb_config:
     ny = nx if ny is None else ny
     nz = nx if nz is None else nz
     return lb_config(int(nx), int(ny), int(nz), float(nu),
                      VARIANT[variant] if isinstance(variant, str) else int(variant),
                      GAMMA[gamma] if isinstance(gamma, str) else int(gamma),
                      STORAGE[storage] if isinstance(storage, str) else int(storage),
-                     SCHEME[scheme] if isinstance(scheme, str) else int(scheme))
+                     SCHEME[scheme] if isinstance(scheme, str) else int(scheme),
+                     EQUILIBRIUM[equilibrium] if isinstance(equilibrium, str) else int(equilibrium))
 
 
 # ---------------------------------------------------------------- 1:1 wrappers of the C ABI
@@ -387,9 +390,9 @@ class Lattice:
     """One periodic box. Device memory is a torch uint8 tensor owned by this object."""
 
     def __init__(self, nx, ny=None, nz=None, nu=1e-3, variant="d+t+q", gamma="estimate",
-                 storage="f32", scheme="pull", stream=None, device=None):
+                 storage="f32", scheme="pull", stream=None, device=None, equilibrium="product"):
         torch = _torch()
-        self.cfg = make_config(nx, ny, nz, nu, variant, gamma, storage, scheme)
+        self.cfg = make_config(nx, ny, nz, nu, variant, gamma, storage, scheme, equilibrium)
         self.shape = (self.cfg.nz, self.cfg.ny, self.cfg.nx)
         self.P = self.cfg.nx * self.cfg.ny * self.cfg.nz
         self.nbytes = lb_required_bytes(self.cfg)
@@ -414,6 +417,10 @@ class Lattice:
     @property
     def t(self) -> int:
         return lb_time(self.ctx)
+
+    @property
+    def nu(self) -> float:
+        return self.cfg.nu
 
     @property
     def beta(self) -> float:

@@ -81,3 +81,14 @@ def test_null_handles_are_rejected(lib):
     assert lib.lb_destroy(None) == 1
     assert lib.lb_batch_step(None, 1) == 1
     assert lib.lb_time(None) == -1
+
+
+def test_equilibrium_choice_is_validated(lib):
+    from paper_1507_02518_gb300 import lb
+    assert lb.lb_required_bytes(lb.make_config(32, equilibrium="poly2")) > 0
+    c = lb.make_config(32)
+    c.equilibrium = 2
+    assert lb.lb_required_bytes(c) == 0
+    with pytest.raises(lb.LBError) as e:     # refused on the host, before any device call
+        lb.lb_create(lb.make_config(32, gamma="exact", equilibrium="poly2"), 256, 1 << 30, 0)
+    assert e.value.status == lb.LB_ERR_UNSUPPORTED
