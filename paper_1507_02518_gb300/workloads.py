@@ -139,6 +139,63 @@ def random_spectrum_device(n: int, k0: float, urms: float, seed: int, device="cu
     return None, u
 
 
+E0_U0P = 0.01           # u0' of eq:E0 (Sec. "Numerical Simulations", second example)
+E0_NU = 8.164970e-5     # nu of eq:E0
+
+
+def spectrum_e0(n: int, u0p: float = E0_U0P, nu: float = E0_NU, seed: int = 1, device="cpu"):
+    """Random solenoidal field whose shell spectrum is eq:E0:
+        E0(kappa) = 400 (2/3)^(1/4) (2 nu u0'^3 / pi)^(1/2) b^2 kappa^4 exp(-b kappa^2),
+        b = 20000 (2/3)^(1/2) nu / u0',
+    kappa in lattice units (2 pi m / n for shell m). White Gaussian noise per component is
+    transformed, projected onto divergence-free modes (mean and Nyquist modes removed), and
+    each shell m = rint(|n|) is rescaled so that it carries exactly E0(kappa_m) d kappa,
+    d kappa = 2 pi / n (so k = sum of the shells, which is 3 u0'^2 / 2 when the peak is
+    resolved). torch (float64) on ``device``; returns (None, u[3, n, n, n]) there."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    f64 = dict(dtype=torch.float64, device=device)
+    kf = torch.fft.fftfreq(n, d=1.0 / n, **f64)
+    kr = torch.fft.rfftfreq(n, d=1.0 / n, **f64)
+    KZ, KY, KX = kf.view(n, 1, 1), kf.view(1, n, 1), kr.view(1, 1, -1)
+    K2 = KX * KX + KY * KY + KZ * KZ
+    shell = torch.round(torch.sqrt(K2)).to(torch.int64)
+    nyq = n // 2
+    keep = ~((KX.abs() == nyq) | (KY.abs() == nyq) | (KZ.abs() == nyq) | (K2 == 0))
+    a = []
+    for _ in range(3):
+        noise = torch.randn((n, n, n), generator=gen, **f64)
+        a.append(torch.fft.rfftn(noise) * keep)
+        del noise
+    safe = torch.where(K2 > 0, K2, torch.ones_like(K2))
+    kdota = (KX * a[0] + KY * a[1] + KZ * a[2]) / safe
+    a = [a[0] - KX * kdota, a[1] - KY * kdota, a[2] - KZ * kdota]
+    del kdota, safe
+    # shell energies of the half spectrum: 1/2 |u_hat|^2, u_hat = rfft / P, doubled off the
+    # kx = 0 and kx = n/2 planes (they stand for the conjugate modes too)
+    P = float(n) ** 3
+    w = torch.full((1, 1, kr.numel()), 2.0, **f64)
+    w[..., 0] = 1.0
+    if n % 2 == 0:
+        w[..., -1] = 1.0
+    e = 0.5 * w * sum((c.abs() ** 2) for c in a) / (P * P)
+    nb = int(shell.max()) + 1
+    E = torch.zeros(nb, **f64).index_add_(0, shell.flatten(), e.expand_as(shell).flatten())
+    b = 20000.0 * math.sqrt(2.0 / 3.0) * nu / u0p
+    kap = 2.0 * math.pi * torch.arange(nb, **f64) / n
+    target = (400.0 * (2.0 / 3.0) ** 0.25 * math.sqrt(2.0 * nu * u0p ** 3 / math.pi) * b * b
+              * kap ** 4 * torch.exp(-b * kap * kap)) * (2.0 * math.pi / n)
+    scale = torch.where(E > 0, torch.sqrt(target / torch.where(E > 0, E, torch.ones_like(E))),
+                        torch.zeros_like(E))
+    sc = scale[shell]
+    u = torch.empty((3, n, n, n), **f64)
+    for c in range(3):
+        u[c] = torch.fft.irfftn(a[c] * sc, s=(n, n, n))
+        a[c] = None
+    return None, u
+
+
 def kida_device(n: int, U0: float = 0.05, device="cuda"):
     """eq:kida on a GPU with torch (float64); returns (None, u[3, n, n, n]) on ``device``."""
     import torch
