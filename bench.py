@@ -66,9 +66,10 @@ VARIANTS = [
      "gamma": "exact", "gap": True},
 ]
 # FP64-pipe instructions per lattice update of step_kernel<double> (ncu: the FP64 pipe was
-# 87.6 % busy, 598 instructions per node; profiles/step_kernel_f64_pull_hit128.md) and the
-# GB300 FP64 pipe peak of 2 instructions per SM per cycle.
-FP64_INSTR_PER_LUP = 598.0
+# 86.8 % busy over 2.19 ms for 2,097,152 nodes, 571 instructions per node;
+# profiles/step_kernel_f64_pull_hit128.md) and the GB300 FP64 pipe peak of 2 instructions per
+# SM per cycle.
+FP64_INSTR_PER_LUP = 571.0
 FP64_PIPE_PER_SM_PER_CYCLE = 2.0
 # DRAM bytes per lattice update of the default FP32 pull step kernel (packed FP32x2) from an ncu
 # capture, keyed by a hash of the kernel sources; a changed kernel gets no traffic figure until

@@ -148,21 +148,26 @@ lb_status lb_init_field(lb_ctx *ctx, const double *rho, const double *u, int on_
 
 /* Consistent initial state (Sec. "Numerical Simulations": the initial density and higher
  * moments come from an iteration run to steady state beforehand, after Mei et al.). Sets
- * f = f_eq(1, u0), then iterates
+ * f = f_eq(1, u0) (unless from_current), then iterates
  *     f <- S[ f - 2 beta_pre (f - f_eq(rho(f), u0)) ],   beta_pre = 1/(6 nu_pre + 1),
  * (S: propagation) with the velocity of the equilibrium held at u0 while the density evolves.
  * Every 32 iterations (and after the last) the largest change of rho over the last iteration
  * is measured, on rho - 1 rounded to FP32; the loop stops when it is <= tol (a negative tol
  * runs max_iters) or after max_iters iterations, rounded up to an even count. The result is
  * the state at t = 0; lb_diagnostics has no gamma until the next lb_step.
- *   u0        FP64 [3][P], host (copied in chunks) or device (on_device != 0)
- *   nu_pre    > 0, the pre-solve's own relaxation (1/6 relaxes fully to f_eq each iteration)
- *   iters     iterations run (may be NULL);  residual  the last measured change (may be NULL;
- *             NaN if max_iters is 0)
+ *   u0            FP64 [3][P], host (copied in chunks) or device (on_device != 0)
+ *   nu_pre        > 0, the pre-solve's own relaxation (1/6 relaxes fully to f_eq each
+ *                 iteration)
+ *   from_current  nonzero: start from the current state instead of f_eq(1, u0), e.g. from
+ *                 lb_init_field(rho_guess, u0) with a density interpolated from a coarser
+ *                 pre-solve; requires t = 0 (LB_ERR_INVALID_ARG otherwise)
+ *   iters         iterations run (may be NULL);  residual  the last measured change (may be
+ *                 NULL; NaN if max_iters is 0)
  * Uses the diagnostics work area and the gamma field as scratch. Synchronises. Returns
  * LB_ERR_NONFINITE if the iteration produced NaN/Inf. */
 lb_status lb_presolve(lb_ctx *ctx, const double *u0, int on_device, double nu_pre,
-                      int64_t max_iters, double tol, int64_t *iters, double *residual);
+                      int64_t max_iters, double tol, int32_t from_current, int64_t *iters,
+                      double *residual);
 
 /* Advance n >= 0 time steps (eq:Egeneral with the KBC collision). Asynchronous. The last of
  * the n collisions also records gamma per node for lb_diagnostics. */

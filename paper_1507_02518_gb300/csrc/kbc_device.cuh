@@ -342,10 +342,16 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, int* g
   const R ux = O::mul(D100, ir), uy = O::mul(D010, ir), uz = O::mul(D001, ir);
 
   // ---- per-axis equilibrium factors (listing step 2): e = R - 1 = 3u^2 / (1 + R)
+  // FP32: 3u^2/(1 + R) avoids the cancellation of R - 1 at small u. FP64: R - 1 directly
+  // (exact subtraction, absolute error ~1e-16, far below what the populations resolve),
+  // which saves a division on GB300's narrow FP64 pipe.
   auto axis_e = [&](R u) {
     const R u3 = O::mul(three, O::mul(u, u));
     const R Rr = O::sqrt_fast(O::add(one, u3));
-    return O::div_fast(u3, O::add(one, Rr));
+    if constexpr (std::is_same<T, double>::value)
+      return O::sub(Rr, one);
+    else
+      return O::div_fast(u3, O::add(one, Rr));
   };
   const R c23 = O::c(2.0 / 3.0), c13 = O::c(1.0 / 3.0);
   // product form: e = R - 1 and the per-axis second moment m_2(u) = (2R - 1)/3 = 1/3 + 2e/3,
@@ -445,20 +451,40 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, int* g
     fz[0] = O::sub(tez, uz3);
     fz[1] = O::neg(ez);
     fz[2] = O::add(tez, uz3);
-    auto recip_axis = [&](const R (&e)[3], R (&r)[3]) {
-      const R p0 = O::mul(c16, O::add(one, e[0]));
-      const R p1 = O::mul(c23, O::add(one, e[1]));
-      const R p2 = O::mul(c16, O::add(one, e[2]));
-      const R p12 = O::mul(p1, p2);
-      const R q = O::div_fast(one, O::mul(p0, p12));   // one division for three reciprocals
-      const R qp0 = O::mul(q, p0);
-      r[0] = O::mul(p12, q);
-      r[1] = O::mul(p2, qp0);
-      r[2] = O::mul(p1, qp0);
+    // per axis: q = 1 / (p0 p1 p2) gives the three reciprocals 1/p_a by products. FP32 takes
+    // one MUFU reciprocal per axis; FP64 shares one IEEE division among the three axes.
+    R px[3], py[3], pz[3], Q[3];
+    auto axis_p = [&](const R (&e)[3], R (&p)[3], R& q) {
+      p[0] = O::mul(c16, O::add(one, e[0]));
+      p[1] = O::mul(c23, O::add(one, e[1]));
+      p[2] = O::mul(c16, O::add(one, e[2]));
+      q = O::mul(p[0], O::mul(p[1], p[2]));
     };
-    recip_axis(gx, rx);
-    recip_axis(fy, ry);
-    recip_axis(fz, rz);
+    axis_p(gx, px, Q[0]);
+    axis_p(fy, py, Q[1]);
+    axis_p(fz, pz, Q[2]);
+    R iq[3];
+    if constexpr (std::is_same<T, double>::value) {
+      const R Q12 = O::mul(Q[1], Q[2]);
+      const R inv = O::div_fast(one, O::mul(Q[0], Q12));
+      const R invQ0 = O::mul(inv, Q[0]);
+      iq[0] = O::mul(inv, Q12);
+      iq[1] = O::mul(invQ0, Q[2]);
+      iq[2] = O::mul(invQ0, Q[1]);
+    } else {
+      iq[0] = O::div_fast(one, Q[0]);
+      iq[1] = O::div_fast(one, Q[1]);
+      iq[2] = O::div_fast(one, Q[2]);
+    }
+    auto recip_axis = [&](const R (&p)[3], R q, R (&r)[3]) {
+      const R qp0 = O::mul(q, p[0]);
+      r[0] = O::mul(O::mul(p[1], p[2]), q);
+      r[1] = O::mul(p[2], qp0);
+      r[2] = O::mul(p[1], qp0);
+    };
+    recip_axis(px, iq[0], rx);
+    recip_axis(py, iq[1], ry);
+    recip_axis(pz, iq[2], rz);
   }
   // eq:polynomial2 with c_s^2 = 1/3: (f_eq_i - W_i)/W_i = drho + rho (3 s + 9/2 s^2 - 3/2 u.u),
   // s = u.v_i

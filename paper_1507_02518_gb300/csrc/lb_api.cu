@@ -356,22 +356,26 @@ lb_status lb_init_field(lb_ctx* c, const double* rho, const double* u, int on_de
 }
 
 lb_status lb_presolve(lb_ctx* c, const double* u0, int on_device, double nu_pre,
-                      int64_t max_iters, double tol, int64_t* iters, double* residual) {
+                      int64_t max_iters, double tol, int32_t from_current, int64_t* iters,
+                      double* residual) {
   if (!c) return LB_ERR_INVALID_ARG;
   if (!u0) return fail(c, LB_ERR_INVALID_ARG, "u0 is NULL");
   if (!(nu_pre > 0.0) || !std::isfinite(nu_pre))
     return fail(c, LB_ERR_INVALID_ARG, "nu_pre must be finite and > 0");
   if (max_iters < 0) return fail(c, LB_ERR_INVALID_ARG, "max_iters must be >= 0");
   if (std::isnan(tol)) return fail(c, LB_ERR_INVALID_ARG, "tol is NaN");
+  if (from_current && c->t != 0)
+    return fail(c, LB_ERR_INVALID_ARG, "from_current needs the state at t = 0");
   const uint64_t P = c->box.P;
   const double beta_pre = 1.0 / (6.0 * nu_pre + 1.0);
   c->t = 0;
   c->gamma_valid = false;
   cudaError_t e = cudaSuccess;
-  // u0 into the diagnostics velocity field (collision precision), f = f_eq(1, u0) at t = 0
+  // u0 into the diagnostics velocity field (collision precision); unless continuing from the
+  // current state, f = f_eq(1, u0) at t = 0
   if (on_device) {
     e = dispatch(c, [&](auto ops) { return ops.convert_u(u0, c->ufield, 0, P, P, P, c->stream); });
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && !from_current)
       e = dispatch(c, [&](auto ops) { return ops.init(c->box, 0, nullptr, u0, 0, P, P, c->stream); });
     if (e != cudaSuccess) return cuda_fail(c, e, "pre-solve set-up");
   } else {
@@ -385,7 +389,7 @@ lb_status lb_presolve(lb_ctx* c, const double* u0, int on_device, double nu_pre,
         e = dispatch(c, [&](auto ops) {
           return ops.convert_u(su, c->ufield, n0, cnt, cnt, P, c->stream);
         });
-      if (e == cudaSuccess)
+      if (e == cudaSuccess && !from_current)
         e = dispatch(c, [&](auto ops) { return ops.init(c->box, 0, nullptr, su, n0, cnt, cnt, c->stream); });
       if (e != cudaSuccess) return cuda_fail(c, e, "pre-solve set-up");
     }

@@ -172,7 +172,7 @@ def load(path: str = LIB_PATH):
         L.lb_set_diag_order.restype = i32
         L.lb_set_diag_order.argtypes = [vp, i32]
         L.lb_presolve.restype = i32
-        L.lb_presolve.argtypes = [vp, vp, ctypes.c_int, d, i64, d, ctypes.POINTER(i64),
+        L.lb_presolve.argtypes = [vp, vp, ctypes.c_int, d, i64, d, i32, ctypes.POINTER(i64),
                                   ctypes.POINTER(d)]
         L.lb_stabilizer_gap.restype = i32
         L.lb_stabilizer_gap.argtypes = [vp, ctypes.POINTER(lb_gap)]
@@ -240,11 +240,12 @@ def lb_set_diag_order(ctx, order: int):
     _check(load().lb_set_diag_order(ctx, int(order)), ctx)
 
 
-def lb_presolve(ctx, u0_ptr: int, on_device: bool, nu_pre: float, max_iters: int, tol: float):
+def lb_presolve(ctx, u0_ptr: int, on_device: bool, nu_pre: float, max_iters: int, tol: float,
+                from_current: bool = False):
     it, res = ctypes.c_int64(), ctypes.c_double()
     _check(load().lb_presolve(ctx, ctypes.c_void_p(u0_ptr), int(on_device), float(nu_pre),
-                              int(max_iters), float(tol), ctypes.byref(it), ctypes.byref(res)),
-           ctx)
+                              int(max_iters), float(tol), int(bool(from_current)),
+                              ctypes.byref(it), ctypes.byref(res)), ctx)
     return it.value, res.value
 
 
@@ -438,15 +439,16 @@ class Lattice:
             r = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64)
             lb_init_field(self.ctx, 0 if r is None else r.ctypes.data, u.ctypes.data, False)
 
-    def presolve(self, u0, nu_pre=1.0 / 6.0, max_iters=20000, tol=1e-9):
+    def presolve(self, u0, nu_pre=1.0 / 6.0, max_iters=20000, tol=1e-9, from_current=False):
         """Consistent initial state for the velocity u0 ([3,nz,ny,nx], numpy or CUDA tensor):
         see lb_presolve. Returns (iterations, last change of rho)."""
         torch = _torch()
         if isinstance(u0, torch.Tensor) and u0.is_cuda:
             u0 = u0.to(torch.float64).contiguous()
-            return lb_presolve(self.ctx, u0.data_ptr(), True, nu_pre, max_iters, tol)
+            return lb_presolve(self.ctx, u0.data_ptr(), True, nu_pre, max_iters, tol,
+                               from_current)
         u0 = np.ascontiguousarray(u0, dtype=np.float64)
-        return lb_presolve(self.ctx, u0.ctypes.data, False, nu_pre, max_iters, tol)
+        return lb_presolve(self.ctx, u0.ctypes.data, False, nu_pre, max_iters, tol, from_current)
 
     def step(self, n=1):
         lb_step(self.ctx, n)

@@ -11,59 +11,15 @@ from the pre-solved state, k within 0.08 %, Omega within 0.17 %, epsilon within 
 Re_lambda and eta within 0.12 %. The odd skewness S3 is a small difference of large terms and
 is only printed. Tolerances: about twice to five times the measured deviation.
 """
-import os
-
-import numpy as np
 import pytest
 
-from paper_1507_02518_gb300 import lb, statistics, workloads
+from paper_1507_02518_gb300 import table2
 
 pytestmark = pytest.mark.gpu
-GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "table2_kida_statistics.txt")
-
-
-def presolved_state(n, U0, storage):
-    """The pre-solved Kida state (FP64 iteration), moved into a lattice of the given storage
-    on the device."""
-    import torch
-    _, u = workloads.kida(n, U0)
-    pre = lb.Lattice(n, storage="f64", scheme="aa")
-    it, res = pre.presolve(u, max_iters=200000, tol=1e-10)
-    print("pre-solve N = %d: %d iterations, last change %.2e" % (n, it, res))
-    assert res <= 1e-10, (it, res)
-    f = torch.empty((27, pre.P), dtype=torch.float64, device="cuda")
-    lb.lb_get_populations(pre.ctx, f.data_ptr(), True)
-    pre.close()
-    return f
 
 
 def run_table2(run, storage, init):
-    n, U0 = statistics.RUNS[run], 0.05
-    nu = U0 * n / 6000.0
-    lat = lb.Lattice(n, nu=nu, storage=storage, scheme="aa", variant="d+t+q")
-    if init == "presolve":
-        f = presolved_state(n, U0, "f64")
-        lb.lb_set_populations(lat.ctx, f.data_ptr(), True)
-        del f
-    else:
-        rho, u = workloads.kida(n, U0)
-        lat.init_field(rho, u)
-    lat.set_diag_order(8)
-    tab = statistics.read_table2(GOLDEN)
-    rows = {}
-    done = 0
-    for t in (0.25, 0.5, 0.75):
-        steps = int(round(t * n / U0))
-        lat.step(steps - done)
-        done = steps
-        d = lat.diagnostics()
-        assert d["nonfinite_count"] == 0
-        rows[t] = statistics.table2_row(d, n, nu)
-        for q in ("k_1e4", "OmegaN2", "epsN_1e5", "S3_1e2", "S4", "Relam", "etaN_1e3"):
-            paper = tab[(q, t)][run]
-            print("Table 2 run %s, %s, %s init: t = %.2f  %-9s %9.4g  paper %9.4g  (%+.2f %%)"
-                  % (run, storage, init, t, q, rows[t][q], paper,
-                     100 * (rows[t][q] / paper - 1)))
+    rows, tab, _ = table2.run_table2(run, storage, init)
     return rows, tab
 
 

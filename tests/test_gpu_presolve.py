@@ -87,3 +87,35 @@ def test_arguments_are_validated(kbc):
         assert e.value.status == lb.LB_ERR_INVALID_ARG
     it, res = lat.presolve(u0, max_iters=0)
     assert it == 0 and np.isnan(res)
+
+
+def test_continuing_from_the_current_state_is_the_same_iteration(kbc):
+    _, u0 = workloads.kida(12, 0.05)
+    a = lattice((12, 12, 12), storage="f64", scheme="aa")
+    a.presolve(u0, max_iters=20, tol=-1.0)
+    b = lattice((12, 12, 12), storage="f64", scheme="aa")
+    b.presolve(u0, max_iters=10, tol=-1.0)
+    b.presolve(u0, max_iters=10, tol=-1.0, from_current=True)
+    assert np.array_equal(a.get_populations(), b.get_populations())
+    b.step(1)
+    with pytest.raises(lb.LBError) as e:
+        b.presolve(u0, max_iters=2, from_current=True)
+    assert e.value.status == lb.LB_ERR_INVALID_ARG
+
+
+def test_interpolated_density_start_converges_to_the_same_state(kbc):
+    """The coarse-to-fine start of the pre-solve (table2.presolved_density) reaches the state a
+    cold start reaches."""
+    import torch
+    from paper_1507_02518_gb300 import table2
+    n = 32
+    _, u = workloads.kida(n, 0.05)
+    cold = lattice((n, n, n), storage="f64", scheme="aa")
+    it_cold, _ = cold.presolve(u, max_iters=100000, tol=1e-13)
+    rho_c = table2.presolved_density(16, "f64", 1e-13, min_n=16, log=lambda *a: None)
+    warm = lattice((n, n, n), storage="f64", scheme="aa")
+    warm.init_field(table2.interpolate_periodic(rho_c, n), torch.from_numpy(u).cuda())
+    it_warm, _ = warm.presolve(u, max_iters=100000, tol=1e-13, from_current=True)
+    print("cold %d iterations, warm %d" % (it_cold, it_warm))
+    assert it_warm < it_cold
+    assert np.max(np.abs(warm.get_populations() - cold.get_populations())) <= 1e-10
