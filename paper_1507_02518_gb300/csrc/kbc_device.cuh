@@ -808,14 +808,23 @@ __device__ __forceinline__ void node_update2(const S* src, S* dst, const Geo& g,
   // In the AA modes the stores reuse the load addresses' planes; opaque copies of P and dst
   // make the compiler recompute the store addresses instead of keeping 27 64-bit addresses
   // live across the collision (which spilled at 3 blocks per SM).
+  // The odd AA step also stores to the 27 neighbours: its neighbour offsets are rebuilt from
+  // opaque copies of the coordinates rather than kept live across the collision.
   uint64_t Ps = g.P;
   S* dsts = dst;
   if constexpr (MODE != MODE_PULL) asm volatile("" : "+l"(Ps), "+l"(dsts));
+  Nbr sa = na, sb = nb;
+  if constexpr (MODE == MODE_AA_ODD) {
+    uint32_t xa2 = xa, xb2 = vb ? xb : xa, y2 = y, z2 = z;
+    asm volatile("" : "+r"(xa2), "+r"(xb2), "+r"(y2), "+r"(z2));
+    sa.init(g, xa2, y2, z2);
+    sb.init(g, xb2, y2, z2);
+  }
   Unroll<0, 27>::run([&](auto ic) {
     constexpr int I = decltype(ic)::value;
     S* base = dsts + (uint64_t)Pat::store_plane(I) * Ps;
-    Codec2<S>::template store<I>(base + na.template at<I, Pat::store_shift>(),
-                                 base + nb.template at<I, Pat::store_shift>(), vb, d[I]);
+    Codec2<S>::template store<I>(base + sa.template at<I, Pat::store_shift>(),
+                                 base + sb.template at<I, Pat::store_shift>(), vb, d[I]);
   });
   if constexpr (RECORD) {
     gamma_out[na.ox[1] + na.oy[1] + na.oz[1]] = gamma.x;
