@@ -18,10 +18,13 @@ __device__ __forceinline__ S* canon_addr(S* b0, S* b1, const Geo& g, const Nbr& 
   return b0 + (uint64_t)(26 - i) * g.P + back;
 }
 
+// (32-bit arithmetic: a box holds fewer than 2^31 nodes; a 64-bit division would be a long
+// software sequence)
 __device__ __forceinline__ void node_coords(const Geo& g, uint64_t n, uint32_t& x, uint32_t& y,
                                             uint32_t& z) {
-  z = (uint32_t)(n / g.nxy);
-  const uint32_t r = (uint32_t)(n - (uint64_t)z * g.nxy);
+  const uint32_t m = (uint32_t)n;
+  z = m / g.nxy;
+  const uint32_t r = m - z * g.nxy;
   y = r / g.nx;
   x = r - y * g.nx;
 }
@@ -169,8 +172,9 @@ __device__ __forceinline__ void node_moments_r(const S* buf, const Geo& g, const
 }
 
 // Per-node quantities in the storage's arithmetic type; block and global sums in FP64.
+// 4 blocks of 256 threads per SM: the fixed grid of 608 blocks is then resident in one wave
 template <typename S, int KIND>
-__global__ void __launch_bounds__(256) diag_fields_kernel(const S* buf, Geo g,
+__global__ void __launch_bounds__(256, 4) diag_fields_kernel(const S* buf, Geo g,
                                                           const float* gamma, int with_gamma,
                                                           typename Codec<S>::R* uf,
                                                           double* partials) {

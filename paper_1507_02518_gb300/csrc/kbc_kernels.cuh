@@ -120,17 +120,29 @@ __global__ void __launch_bounds__(128, 3) batch_pair_kernel(const BoxDesc* __res
     cp.gamma_mode = gamma_mode;
     const S* src = (const S*)bd.pop[MODE == MODE_PULL ? parity : 0];
     S* dst = (S*)bd.pop[MODE == MODE_PULL ? (parity ^ 1) : 0];
+    // warp q of the item handles 64-node chunk (q mod nchunk) of row (q / nchunk); the warp
+    // index advances by the block's warp count, and chunk, y and z follow it incrementally
+    // (no integer division per unit). blockDim.x is 128 for this kernel.
     const uint32_t nchunk = (bd.nx + 63) / 64;
-    const uint32_t units = (uint32_t)w.nrows * nchunk * 32;
-    for (uint32_t u = threadIdx.x; u < units; u += blockDim.x) {
-      const uint32_t slot = u & 31, q = u >> 5;
-      const uint32_t rr = q / nchunk, chunk = q - rr * nchunk;
-      const uint32_t row = (uint32_t)w.row0 + rr;
-      const uint32_t z = row / bd.ny, y = row - z * bd.ny;
+    const uint32_t nq = (uint32_t)w.nrows * nchunk;
+    const uint32_t wstep = blockDim.x >> 5, slot = threadIdx.x & 31;
+    uint32_t q = threadIdx.x >> 5;
+    uint32_t rr = q / nchunk, chunk = q - rr * nchunk;
+    const uint32_t row = (uint32_t)w.row0 + rr;
+    uint32_t z = row / bd.ny, y = row - z * bd.ny;
+    for (; q < nq; q += wstep) {
       const uint32_t xa = chunk * 64 + slot, xb = xa + 32;
       if (xa < bd.nx)
         node_update2<S, MODE, RECORD, CENTRAL>(src, dst, g, xa, xb, xb < bd.nx, y, z, cp,
                                                bd.gamma, bd.ctr);
+      chunk += wstep;
+      while (chunk >= nchunk) {
+        chunk -= nchunk;
+        if (++y == bd.ny) {
+          y = 0;
+          ++z;
+        }
+      }
     }
   }
 }

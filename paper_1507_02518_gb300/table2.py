@@ -47,6 +47,47 @@ def interpolate_periodic(field, n):
     return torch.fft.irfftn(G, s=(n, n, n)) * (float(n) / m) ** 3
 
 
+def restrict_periodic(field, m):
+    """Spectral truncation of a periodic field [..., n, n, n] (torch, float64) to [..., m, m, m],
+    m <= n: the modes -h..h, h = (m - 1) // 2, in each direction."""
+    import torch
+    n = field.shape[-1]
+    if m == n:
+        return field.clone()
+    F = torch.fft.rfftn(field, dim=(-3, -2, -1))
+    h = (m - 1) // 2
+    G = torch.zeros(field.shape[:-3] + (m, m, m // 2 + 1), dtype=F.dtype, device=F.device)
+    for zs, zd in ((slice(0, h + 1), slice(0, h + 1)), (slice(n - h, n), slice(m - h, m))):
+        for ys, yd in ((slice(0, h + 1), slice(0, h + 1)), (slice(n - h, n), slice(m - h, m))):
+            G[..., zd, yd, : h + 1] = F[..., zs, ys, : h + 1]
+    return torch.fft.irfftn(G, s=(m, m, m), dim=(-3, -2, -1)) * (float(m) / n) ** 3
+
+
+def presolved_density_of(u, storage="f32", tol=2e-9, min_n=100, log=print):
+    """rho [n, n, n] (torch float64 on the GPU) of the pre-solved state for the velocity field
+    u [3, n, n, n] (torch float64 on the GPU), built coarse to fine: the pre-solve of the
+    spectrally truncated field on the n/2 box seeds the one on the n box."""
+    import torch
+    n = u.shape[-1]
+    lat = lb.Lattice(n, storage=storage, scheme="aa")
+    from_current = False
+    if n >= 2 * min_n and n % 2 == 0:
+        rho_c = presolved_density_of(restrict_periodic(u, n // 2), storage, tol, min_n, log)
+        lat.init_field(interpolate_periodic(rho_c, n), u)
+        del rho_c
+        from_current = True
+    t0 = time.perf_counter()
+    it, res = lat.presolve(u, tol=tol, max_iters=400000, from_current=from_current)
+    log("pre-solve N = %d (%s, %s): %d iterations, last change %.2e, %.1f s"
+        % (n, storage, "from the N/2 density" if from_current else "from rho = 1", it, res,
+           time.perf_counter() - t0))
+    rho = torch.empty((n, n, n), dtype=torch.float64, device="cuda")
+    uu = torch.empty((3, n, n, n), dtype=torch.float64, device="cuda")
+    lb.lb_moments(lat.ctx, rho.data_ptr(), uu.data_ptr(), True)
+    lat.close()
+    return rho
+
+
 def presolved_density(n, storage="f32", tol=2e-9, min_n=100, log=print):
     """rho [n, n, n] (torch float64 on the GPU) of the pre-solved Kida state, built coarse to
     fine from min_n upward by factors of 2 when n allows it."""
