@@ -29,10 +29,14 @@ import numpy as np
 from . import lb, workloads
 
 
-def _field(kind, n, seed, device):
+def _field(kind, n, seed, device, urms=0.04):
     import torch
+    if kind == "spectrum" and n > 256:
+        return workloads.random_spectrum_device(n, 4.0, urms, seed, device)[1]
+    if kind == "kida" and n > 256:
+        return workloads.kida_device(n, 0.05, device)[1]
     if kind == "spectrum":
-        rho, u = workloads.random_spectrum(n, 4.0, 0.04, seed)
+        rho, u = workloads.random_spectrum(n, 4.0, urms, seed)
     elif kind == "kida":
         rho, u = workloads.kida(n, 0.05)
     else:
@@ -89,10 +93,11 @@ def compare(ref, other):
 
 
 def study(n=256, steps=2000, every=50, field="spectrum", nu=2e-4, stride=1, seed=1,
-          precisions=(("f32", "pull"), ("f32", "aa"), ("f16", "aa")), ref_scheme="aa"):
+          precisions=(("f32", "pull"), ("f32", "aa"), ("f16", "aa")), ref_scheme="aa",
+          urms=0.04):
     import torch
     lb.load()
-    u = _field(field, n, seed, "cuda")
+    u = _field(field, n, seed, "cuda", urms)
     ref = run_one(n, "f64", ref_scheme, nu, u, steps, every, stride)
     res = {"n": n, "steps": steps, "every": every, "field": field, "nu": nu, "stride": stride,
            "reference": {"storage": "f64", "scheme": ref_scheme, "wall_s": ref["wall_s"],
@@ -117,9 +122,12 @@ def main(argv=None):
     p.add_argument("--field", choices=["spectrum", "kida"], default="spectrum")
     p.add_argument("--nu", type=float, default=2e-4)
     p.add_argument("--stride", type=int, default=1)
+    p.add_argument("--urms", type=float, default=0.04)
+    p.add_argument("--precisions", default="f32:pull,f32:aa,f16:aa")
     p.add_argument("--out", default=None)
     a = p.parse_args(argv)
-    res = study(a.n, a.steps, a.every, a.field, a.nu, a.stride)
+    precs = tuple(tuple(x.split(":")) for x in a.precisions.split(","))
+    res = study(a.n, a.steps, a.every, a.field, a.nu, a.stride, precisions=precs, urms=a.urms)
     text = json.dumps(res, indent=1)
     if a.out:
         with open(a.out, "w") as fh:
