@@ -22,6 +22,7 @@ import os
 import signal
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -177,7 +178,9 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % index)
+        # the samples of the last run stay in the system temp folder (or BENCH_CLOCKS_DIR)
+        folder = os.environ.get("BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(folder, "kbc_bench_clocks_rank%d.csv" % index)
 
     def __enter__(self):
         try:

@@ -3,7 +3,9 @@
 Tolerances:
   * FP64 storage: max |df| <= 1e-12 after 100 steps (the stated FP64 bar).
   * FP32 storage, one step from identical stored inputs: every population within
-    FP32_STEP_TOL (derived from FP32 round-off of the collision) of the oracle.
+    FP32_STEP_TOL of the oracle: the collision works on shifts |f - W| <~ 0.05 with ~50
+    rounded operations per output at a unit round-off of 6e-8 relative to operands <~ W ~ 0.3,
+    a few 1e-8 typically and 2e-7 as a bound, plus the storage rounding.
   * FP16 storage, one step: the stored half of (f - W)/W equals the oracle's result rounded
     to half, or is one half-ulp away (the two sides round values that differ by FP32 error).
   * Index/layout work (set/get round trips, pull vs AA, batch vs single box, checkpoints):
