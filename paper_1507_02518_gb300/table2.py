@@ -113,14 +113,17 @@ def presolved_density(n, storage="f32", tol=2e-9, min_n=100, log=print):
 
 
 def run_table2(run, storage="f32", init="presolve", presolve_storage="f64", tol=1e-10,
-               coarse=False, log=print):
-    """Runs one column of Table 2; returns ({t: row}, table, info)."""
+               coarse=False, log=print, equilibrium="product"):
+    """Runs one column of Table 2; returns ({t: row}, table, info). equilibrium: product
+    (eq:entropic_eq) or poly2 (eq:polynomial2) for the collision."""
     import torch
     n = statistics.RUNS[run]
     nu = U0 * n / 6000.0
     gamma = "lbgk" if run == "D" else "estimate"
-    info = {"run": run, "n": n, "storage": storage, "init": init, "gamma": gamma}
-    lat = lb.Lattice(n, nu=nu, storage=storage, scheme="aa", variant="d+t+q", gamma=gamma)
+    info = {"run": run, "n": n, "storage": storage, "init": init, "gamma": gamma,
+            "equilibrium": equilibrium}
+    lat = lb.Lattice(n, nu=nu, storage=storage, scheme="aa", variant="d+t+q", gamma=gamma,
+                     equilibrium=equilibrium)
     t0 = time.perf_counter()
     if init == "presolve":
         _, u = workloads.kida_device(n, U0)
@@ -176,9 +179,11 @@ def main(argv=None):
     p.add_argument("--tol", type=float, default=1e-10)
     p.add_argument("--coarse", action="store_true",
                    help="start the pre-solve from the interpolated N/2 density")
+    p.add_argument("--equilibrium", default="product", choices=["product", "poly2"])
     p.add_argument("--out", default=None)
     a = p.parse_args(argv)
-    rows, tab, info = run_table2(a.run, a.storage, a.init, a.presolve_storage, a.tol, a.coarse)
+    rows, tab, info = run_table2(a.run, a.storage, a.init, a.presolve_storage, a.tol, a.coarse,
+                                 equilibrium=a.equilibrium)
     dev = {str(t): {q: round(100 * (row[q] / tab[(q, t)][a.run] - 1), 3) for q in QUANTITIES}
            for t, row in rows.items()}
     out = {"info": info, "rows": {str(t): r for t, r in rows.items()}, "deviation_pct": dev}
