@@ -3,6 +3,7 @@
 // launch-shape autotuner. The library allocates no device memory: every region below is
 // carved out of the caller's buffer.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cmath>
 #include <cstdio>
@@ -14,6 +15,17 @@
 
 #include "kbc_lb.h"
 #include "kbc_ops.h"
+
+namespace {
+// NVTX range over one library call (host-side span; a profiler that records NVTX shows the
+// kernels it enqueued under it; without one attached the calls cost a few nanoseconds)
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
+}  // namespace
 
 namespace {
 
@@ -327,6 +339,7 @@ const char* lb_last_error(const lb_ctx* c) {
 }
 
 lb_status lb_init_field(lb_ctx* c, const double* rho, const double* u, int on_device) {
+  Range range_("lb_init_field");
   if (!c) return LB_ERR_INVALID_ARG;
   if (!u) return fail(c, LB_ERR_INVALID_ARG, "u is NULL");
   const uint64_t P = c->box.P;
@@ -358,6 +371,7 @@ lb_status lb_init_field(lb_ctx* c, const double* rho, const double* u, int on_de
 lb_status lb_presolve(lb_ctx* c, const double* u0, int on_device, double nu_pre,
                       int64_t max_iters, double tol, int32_t from_current, int64_t* iters,
                       double* residual) {
+  Range range_("lb_presolve");
   if (!c) return LB_ERR_INVALID_ARG;
   if (!u0) return fail(c, LB_ERR_INVALID_ARG, "u0 is NULL");
   if (!(nu_pre > 0.0) || !std::isfinite(nu_pre))
@@ -446,6 +460,7 @@ lb_status lb_presolve(lb_ctx* c, const double* u0, int on_device, double nu_pre,
 }
 
 lb_status lb_step(lb_ctx* c, int64_t n) {
+  Range range_("lb_step");
   if (!c) return LB_ERR_INVALID_ARG;
   if (n < 0) return fail(c, LB_ERR_INVALID_ARG, "n must be >= 0");
   for (int64_t k = 0; k < n; ++k) {
@@ -464,6 +479,7 @@ lb_status lb_step(lb_ctx* c, int64_t n) {
 }
 
 lb_status lb_moments(lb_ctx* c, double* rho, double* u, int on_device) {
+  Range range_("lb_moments");
   if (!c) return LB_ERR_INVALID_ARG;
   if (!u) return fail(c, LB_ERR_INVALID_ARG, "u is NULL");
   const uint64_t P = c->box.P;
@@ -490,6 +506,7 @@ lb_status lb_moments(lb_ctx* c, double* rho, double* u, int on_device) {
 }
 
 lb_status lb_diagnostics(lb_ctx* c, lb_diag* out) {
+  Range range_("lb_diagnostics");
   if (!c || !out) return c ? fail(c, LB_ERR_INVALID_ARG, "out is NULL") : LB_ERR_INVALID_ARG;
   cudaError_t e = dispatch(c, [&](auto ops) {
     return ops.diag(c->box, c->t, c->gamma_valid, c->diag_order, c->ufield, c->partials,
@@ -560,6 +577,7 @@ size_t lb_spectrum_work_bytes(lb_ctx* c, int32_t nbins) {
 }
 
 lb_status lb_spectrum(lb_ctx* c, void* work, size_t work_bytes, int32_t nbins, double* E) {
+  Range range_("lb_spectrum");
   if (!c) return LB_ERR_INVALID_ARG;
   if (!work || !E) return fail(c, LB_ERR_INVALID_ARG, "work or E is NULL");
   lb_status st;
@@ -588,6 +606,7 @@ lb_status lb_set_diag_order(lb_ctx* c, int32_t order) {
 }
 
 lb_status lb_stabilizer_gap(lb_ctx* c, lb_gap* out) {
+  Range range_("lb_stabilizer_gap");
   if (!c || !out) return c ? fail(c, LB_ERR_INVALID_ARG, "out is NULL") : LB_ERR_INVALID_ARG;
   if (c->box.poly)
     return fail(c, LB_ERR_UNSUPPORTED, "the stabilizer gap is built for the product-form "
@@ -614,6 +633,7 @@ lb_status lb_stabilizer_gap(lb_ctx* c, lb_gap* out) {
 }
 
 lb_status lb_get_populations(lb_ctx* c, double* f, int on_device) {
+  Range range_("lb_get_populations");
   if (!c) return LB_ERR_INVALID_ARG;
   if (!f) return fail(c, LB_ERR_INVALID_ARG, "f is NULL");
   const uint64_t P = c->box.P;
@@ -636,6 +656,7 @@ lb_status lb_get_populations(lb_ctx* c, double* f, int on_device) {
 }
 
 lb_status lb_set_populations(lb_ctx* c, const double* f, int on_device) {
+  Range range_("lb_set_populations");
   if (!c) return LB_ERR_INVALID_ARG;
   if (!f) return fail(c, LB_ERR_INVALID_ARG, "f is NULL");
   const uint64_t P = c->box.P;
@@ -1011,6 +1032,7 @@ lb_ctx* lb_batch_box(lb_batch* b, int32_t box) {
 }
 
 lb_status lb_batch_step(lb_batch* b, int64_t n) {
+  Range range_("lb_batch_step");
   if (!b) return LB_ERR_INVALID_ARG;
   if (n < 0) return bfail(b, LB_ERR_INVALID_ARG, "n must be >= 0");
   if (n == 0) return LB_OK;

@@ -453,6 +453,34 @@ class Lattice:
     def step(self, n=1):
         lb_step(self.ctx, n)
 
+    def run(self, steps, every=50, log=None):
+        """Advance `steps` steps with lb_diagnostics every `every` steps (and at the end).
+        Returns the list of diagnostics dicts, each with the MLUPS of its interval (wall clock
+        between two synchronising diagnostics); with `log`, also appends them as JSON lines."""
+        import json
+        import time
+        out = []
+        fh = open(log, "a") if log else None
+        try:
+            done = 0
+            t0 = time.perf_counter()
+            while done < steps:
+                c = min(every, steps - done)
+                lb_step(self.ctx, c)
+                done += c
+                d = lb_diagnostics(self.ctx, raise_nonfinite=False).as_dict()
+                t1 = time.perf_counter()
+                d["mlups"] = self.P * c / max(t1 - t0, 1e-12) / 1e6
+                t0 = t1
+                out.append(d)
+                if fh:
+                    fh.write(json.dumps(d) + "\n")
+                    fh.flush()
+        finally:
+            if fh:
+                fh.close()
+        return out
+
     def moments(self):
         rho = np.empty(self.shape)
         u = np.empty((3,) + self.shape)

@@ -598,3 +598,17 @@ def test_max_size_768cubed_fp16_aa_sampled_parity(kbc):
     rng = np.random.default_rng(1)
     _sampled_step_check(lat, 24, FP32_STEP_TOL, rng, half=True)     # the odd step t = 3 -> 4
     _sampled_step_check(lat, 24, FP32_STEP_TOL, rng, half=True)     # the even step t = 4 -> 5
+
+
+def test_run_logs_diagnostics_as_json_lines(kbc, tmp_path):
+    import json
+    lat = lattice((16, 16, 16), storage="f32", scheme="aa")
+    rho, u = workloads.taylor_green(16, 0.05)
+    lat.init_field(rho, u)
+    log = tmp_path / "diag.jsonl"
+    out = lat.run(120, every=50, log=str(log))
+    assert [d["step"] for d in out] == [50, 100, 120]
+    lines = [json.loads(l) for l in log.read_text().splitlines()]
+    assert [d["step"] for d in lines] == [50, 100, 120]
+    assert all(d["mlups"] > 0 and d["nonfinite_count"] == 0 for d in lines)
+    assert lines[-1]["kinetic_energy"] < lines[0]["kinetic_energy"]
