@@ -145,3 +145,25 @@ def test_skewness_factors_of_a_two_mode_wave_match_the_continuum():
         assert d["skewness"][i] == pytest.approx(expect, rel=1e-5, abs=1e-9), (m, expect)
     # by hand: <g^2> = 1, <g^3> = 3 <cos^2 th cos 2th> = 3/4, so S3 = -3/4
     assert d["skewness"][0] == pytest.approx(-0.75, rel=1e-5)
+
+
+def test_shear_wave_viscosity_converges_at_second_order():
+    """The lattice's effective viscosity approaches nu as (grid spacing)^2 (the paper's
+    second-order convergence): the relative error of the fitted decay rate falls by ~4 per
+    doubling of the wave's resolution, over the same fraction of its decay time."""
+    nu = 0.01
+    b = oracle.beta(nu)
+    errs = []
+    for ny in (16, 32, 64):
+        rho, u = wl.shear_wave(3, ny, 3, 1e-5)
+        f = oracle.init_equilibrium(rho, u)
+        T = int(0.2 * ny * ny / nu / (4 * math.pi ** 2))
+        f, _, _ = oracle.run(f, T // 4, b)
+        a0 = shear_amplitude(f, ny)
+        f, _, _ = oracle.run(f, T, b)
+        a1 = shear_amplitude(f, ny)
+        k = 2 * math.pi / ny
+        errs.append(abs(-math.log(a1 / a0) / (k * k * T) / nu - 1))
+    assert errs[2] < 2e-3
+    for r in (errs[0] / errs[1], errs[1] / errs[2]):
+        assert 3.3 < r < 4.7, errs
