@@ -36,3 +36,27 @@ def shard_boxes(boxes, rank: int, world: int):
     """The boxes (and their global indices) that `rank` of `world` steps."""
     mine = lpt_assign([box_cost(b) for b in boxes], world)[rank]
     return [boxes[b] for b in mine], mine
+
+
+# ---------------------------------------------------------------- slab decomposition of one box
+# A single box split along z into one slab of whole planes per rank. Collision is local; the
+# propagation of eq:Egeneral needs, across each slab face, the post-collision populations that
+# cross it: the 9 directions with v_z = +1 leave the top plane upwards and the 9 with v_z = -1
+# leave the bottom plane downwards (velocity index i = (vx+1) + 3(vy+1) + 9(vz+1)).
+UP = tuple(range(18, 27))      # v_z = +1
+DOWN = tuple(range(0, 9))      # v_z = -1
+
+
+def slab_bounds(nz: int, rank: int, world: int):
+    """Planes [z0, z1) of `rank`'s slab: nz split as evenly as possible, the first nz % world
+    ranks holding one plane more."""
+    if world < 1 or not 0 <= rank < world or nz < world:
+        raise ValueError("need 0 <= rank < world <= nz")
+    q, r = divmod(nz, world)
+    z0 = rank * q + min(rank, r)
+    return z0, z0 + q + (1 if rank < r else 0)
+
+
+def slab_neighbours(rank: int, world: int):
+    """(rank below, rank above) on the periodic ring of slabs."""
+    return (rank - 1) % world, (rank + 1) % world
