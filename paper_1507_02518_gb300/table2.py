@@ -63,53 +63,48 @@ def restrict_periodic(field, m):
     return torch.fft.irfftn(G, s=(m, m, m), dim=(-3, -2, -1)) * (float(m) / n) ** 3
 
 
+def _presolved(u, rho_start, storage, tol, log):
+    """Pre-solves the velocity field u [3, n, n, n] (torch float64 on the GPU), from rho = 1 or,
+    when rho_start [m, m, m] is given, continuing from its spectral interpolation to n; returns
+    the pre-solved density [n, n, n] (torch float64 on the GPU)."""
+    import torch
+    n = u.shape[-1]
+    lat = lb.Lattice(n, storage=storage, scheme="aa")
+    from_current = rho_start is not None
+    if from_current:
+        lat.init_field(interpolate_periodic(rho_start, n), u)
+    t0 = time.perf_counter()
+    it, res = lat.presolve(u, tol=tol, max_iters=400000, from_current=from_current)
+    log("pre-solve N = %d (%s, %s): %d iterations, last change %.2e, %.1f s"
+        % (n, storage, "from the N/2 density" if from_current else "from rho = 1", it, res,
+           time.perf_counter() - t0))
+    rho = torch.empty((n, n, n), dtype=torch.float64, device="cuda")
+    uu = torch.empty((3, n, n, n), dtype=torch.float64, device="cuda")
+    lb.lb_moments(lat.ctx, rho.data_ptr(), uu.data_ptr(), True)
+    lat.close()
+    return rho
+
+
 def presolved_density_of(u, storage="f32", tol=2e-9, min_n=100, log=print):
     """rho [n, n, n] (torch float64 on the GPU) of the pre-solved state for the velocity field
     u [3, n, n, n] (torch float64 on the GPU), built coarse to fine: the pre-solve of the
     spectrally truncated field on the n/2 box seeds the one on the n box."""
-    import torch
     n = u.shape[-1]
-    lat = lb.Lattice(n, storage=storage, scheme="aa")
-    from_current = False
+    rho_c = None
     if n >= 2 * min_n and n % 2 == 0:
         rho_c = presolved_density_of(restrict_periodic(u, n // 2), storage, tol, min_n, log)
-        lat.init_field(interpolate_periodic(rho_c, n), u)
-        del rho_c
-        from_current = True
-    t0 = time.perf_counter()
-    it, res = lat.presolve(u, tol=tol, max_iters=400000, from_current=from_current)
-    log("pre-solve N = %d (%s, %s): %d iterations, last change %.2e, %.1f s"
-        % (n, storage, "from the N/2 density" if from_current else "from rho = 1", it, res,
-           time.perf_counter() - t0))
-    rho = torch.empty((n, n, n), dtype=torch.float64, device="cuda")
-    uu = torch.empty((3, n, n, n), dtype=torch.float64, device="cuda")
-    lb.lb_moments(lat.ctx, rho.data_ptr(), uu.data_ptr(), True)
-    lat.close()
-    return rho
+    return _presolved(u, rho_c, storage, tol, log)
 
 
 def presolved_density(n, storage="f32", tol=2e-9, min_n=100, log=print):
     """rho [n, n, n] (torch float64 on the GPU) of the pre-solved Kida state, built coarse to
-    fine from min_n upward by factors of 2 when n allows it."""
-    import torch
-    _, u = workloads.kida_device(n, U0)
-    lat = lb.Lattice(n, storage=storage, scheme="aa")
-    from_current = False
+    fine from min_n upward by factors of 2 when n allows it (each level from the Kida field
+    sampled on its own box)."""
+    rho_c = None
     if n >= 2 * min_n and n % 2 == 0:
         rho_c = presolved_density(n // 2, storage, tol, min_n, log)
-        lat.init_field(interpolate_periodic(rho_c, n), u)
-        del rho_c
-        from_current = True
-    t0 = time.perf_counter()
-    it, res = lat.presolve(u, tol=tol, max_iters=400000, from_current=from_current)
-    log("pre-solve N = %d (%s, %s): %d iterations, last change %.2e, %.1f s"
-        % (n, storage, "from the N/2 density" if from_current else "from rho = 1", it, res,
-           time.perf_counter() - t0))
-    rho = torch.empty((n, n, n), dtype=torch.float64, device="cuda")
-    uu = torch.empty((3, n, n, n), dtype=torch.float64, device="cuda")
-    lb.lb_moments(lat.ctx, rho.data_ptr(), uu.data_ptr(), True)
-    lat.close()
-    return rho
+    _, u = workloads.kida_device(n, U0)
+    return _presolved(u, rho_c, storage, tol, log)
 
 
 def run_table2(run, storage="f32", init="presolve", presolve_storage="f64", tol=1e-10,
