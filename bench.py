@@ -303,10 +303,10 @@ def run_batch(w, steps, warmup, rank=0, world=1):
     torch.cuda.synchronize()
     st = batch.stream
     a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    batch.step(steps)                             # capture the graph for this step count
+    batch.step(steps)                             # capture the graphs for this step count
     torch.cuda.synchronize()
     a.record(st)
-    batch.step(steps)                             # replay: one graph launch, `steps` kernels
+    batch.step(steps)                             # replay: one graph launch per 64 steps
     b_.record(st)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b_)

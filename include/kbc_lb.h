@@ -295,8 +295,9 @@ const char *lb_batch_last_error(const lb_batch *b);
  * populations). Valid until lb_batch_destroy; do not lb_destroy it. Its lb_step steps that
  * box alone. */
 lb_ctx *lb_batch_box(lb_batch *b, int32_t box);
-/* Advance every box n >= 0 steps by replaying the captured graph (captured on first use
- * for this n). Asynchronous. */
+/* Advance every box n >= 0 steps by replaying CUDA graphs of at most 64 steps each (each
+ * captured on first use for its length and step parity, so at most 130 graphs are kept).
+ * Asynchronous. LB_ERR_OOM if host memory runs out while capturing. */
 lb_status lb_batch_step(lb_batch *b, int64_t n);
 /* Diagnostics of every box into out[nbox]. Synchronises. */
 lb_status lb_batch_diagnostics(lb_batch *b, lb_diag *out);

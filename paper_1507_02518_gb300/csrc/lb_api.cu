@@ -9,6 +9,8 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <memory>
+#include <new>
 #include <string>
 #include <utility>
 #include <vector>
@@ -34,6 +36,22 @@ thread_local std::string g_create_error;
 constexpr size_t kAlign = 256;
 constexpr uint64_t kStageNodes = 1ull << 20;  // host-transfer chunk (nodes)
 constexpr int32_t kMaxSpectrumBins = 6144;     // shared-memory histogram of 48 KB
+constexpr int64_t kGraphSteps = 64;  // steps per captured batch graph (even: the chunks of one
+                                     // call then share the parity of their first step)
+
+// Runs f(), turning a host allocation failure into LB_ERR_OOM so that no C++ exception
+// crosses the C ABI.
+template <typename F> lb_status no_throw(F&& f) {
+  try {
+    return f();
+  } catch (const std::bad_alloc&) {
+    try {
+      g_create_error = "host memory allocation failed";
+    } catch (...) {
+    }
+    return LB_ERR_OOM;
+  }
+}
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
@@ -281,50 +299,52 @@ size_t lb_required_bytes(const lb_config* cfg) {
 
 lb_status lb_create(const lb_config* cfg, void* dev_buf, size_t bytes, void* stream,
                     lb_ctx** out) {
-  if (!out) {
-    g_create_error = "out is NULL";
-    return LB_ERR_INVALID_ARG;
-  }
-  *out = nullptr;
-  std::string why;
-  if (!valid_config(cfg, &why)) {
-    g_create_error = why;
-    return LB_ERR_INVALID_ARG;
-  }
-  if (cfg->equilibrium == LB_EQ_POLY2 && cfg->gamma_mode == LB_GAMMA_EXACT) {
-    g_create_error = "the exact stabilizer is built for the product-form equilibrium only";
-    return LB_ERR_UNSUPPORTED;
-  }
-  if (!dev_buf || ((uintptr_t)dev_buf % kAlign) != 0) {
-    g_create_error = "dev_buf must be a non-NULL 256-byte aligned device pointer";
-    return LB_ERR_INVALID_ARG;
-  }
-  const size_t need = lb_required_bytes(cfg);
-  if (bytes < need) {
-    char buf[160];
-    snprintf(buf, sizeof buf, "buffer of %zu bytes is smaller than the %zu bytes required", bytes,
-             need);
-    g_create_error = buf;
-    return LB_ERR_OOM;
-  }
-  lb_status s = check_device(&why);
-  if (s != LB_OK) {
-    g_create_error = why;
-    return s;
-  }
-  lb_ctx* c = new lb_ctx();
-  char* base = (char*)dev_buf;
-  const BoxLayout B = box_layout(cfg, 0);
-  const SharedLayout S = shared_layout(cfg->storage, (uint64_t)cfg->nx * cfg->ny * cfg->nz, B.total);
-  setup_ctx(c, cfg, base, B, S, (cudaStream_t)stream);
-  s = zero_state(c);
-  if (s != LB_OK) {
-    g_create_error = c->err;
-    delete c;
-    return s;
-  }
-  *out = c;
-  return LB_OK;
+  return no_throw([&]() -> lb_status {
+    if (!out) {
+      g_create_error = "out is NULL";
+      return LB_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    std::string why;
+    if (!valid_config(cfg, &why)) {
+      g_create_error = why;
+      return LB_ERR_INVALID_ARG;
+    }
+    if (cfg->equilibrium == LB_EQ_POLY2 && cfg->gamma_mode == LB_GAMMA_EXACT) {
+      g_create_error = "the exact stabilizer is built for the product-form equilibrium only";
+      return LB_ERR_UNSUPPORTED;
+    }
+    if (!dev_buf || ((uintptr_t)dev_buf % kAlign) != 0) {
+      g_create_error = "dev_buf must be a non-NULL 256-byte aligned device pointer";
+      return LB_ERR_INVALID_ARG;
+    }
+    const size_t need = lb_required_bytes(cfg);
+    if (bytes < need) {
+      char buf[160];
+      snprintf(buf, sizeof buf, "buffer of %zu bytes is smaller than the %zu bytes required", bytes,
+               need);
+      g_create_error = buf;
+      return LB_ERR_OOM;
+    }
+    lb_status s = check_device(&why);
+    if (s != LB_OK) {
+      g_create_error = why;
+      return s;
+    }
+    lb_ctx* c = new lb_ctx();
+    char* base = (char*)dev_buf;
+    const BoxLayout B = box_layout(cfg, 0);
+    const SharedLayout S = shared_layout(cfg->storage, (uint64_t)cfg->nx * cfg->ny * cfg->nz, B.total);
+    setup_ctx(c, cfg, base, B, S, (cudaStream_t)stream);
+    s = zero_state(c);
+    if (s != LB_OK) {
+      g_create_error = c->err;
+      delete c;
+      return s;
+    }
+    *out = c;
+    return LB_OK;
+  });
 }
 
 lb_status lb_destroy(lb_ctx* c) {
@@ -905,6 +925,52 @@ cudaError_t enqueue_batch_step(lb_batch* b, int64_t t, bool record, cudaStream_t
   }
 }
 
+// The instantiated graph of `len` batch steps from the batch's current time (only its parity
+// matters to the kernels); `record` makes the last of them record gamma and the guard count.
+// Captured on first use and cached.
+lb_status batch_graph(lb_batch* b, int64_t len, bool record, cudaGraphExec_t* out) {
+  const auto key = std::make_pair(len, (int)(b->t & 1) | (record ? 2 : 0));
+  auto it = b->graphs.find(key);
+  if (it != b->graphs.end()) {
+    *out = it->second;
+    return LB_OK;
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess)
+    return bfail(b, LB_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+  cudaError_t le = cudaSuccess;
+  for (int64_t k = 0; k < len; ++k) {
+    const bool rec = record && (k == len - 1);
+    if (rec) {
+      for (lb_ctx* v : b->views)
+        if (le == cudaSuccess)
+          le = cudaMemsetAsync(&v->counters->guarded, 0, sizeof(unsigned long long),
+                               b->capture_stream);
+    }
+    if (le == cudaSuccess) le = enqueue_batch_step(b, b->t + k, rec, b->capture_stream);
+  }
+  e = cudaStreamEndCapture(b->capture_stream, &graph);
+  if (le != cudaSuccess || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return bfail(b, LB_ERR_CUDA, std::string("capturing batch steps: ") +
+                                     cudaGetErrorString(le != cudaSuccess ? le : e));
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess)
+    return bfail(b, LB_ERR_CUDA, std::string("instantiating graph: ") + cudaGetErrorString(e));
+  try {
+    b->graphs.emplace(key, exec);
+  } catch (...) {
+    cudaGraphExecDestroy(exec);
+    throw;
+  }
+  *out = exec;
+  return LB_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -918,99 +984,108 @@ size_t lb_batch_required_bytes(const lb_config* cfgs, int32_t nbox) {
 
 lb_status lb_batch_create(const lb_config* cfgs, int32_t nbox, void* dev_buf, size_t bytes,
                           void* stream, lb_batch** out) {
-  if (!out) {
-    g_create_error = "out is NULL";
-    return LB_ERR_INVALID_ARG;
-  }
-  *out = nullptr;
-  BatchLayout L;
-  std::string why;
-  if (!batch_layout(cfgs, nbox, &L, &why)) {
-    g_create_error = why;
-    return LB_ERR_INVALID_ARG;
-  }
-  if (cfgs[0].gamma_mode == LB_GAMMA_EXACT) {
-    g_create_error = "the batch kernels do not implement the exact stabilizer";
-    return LB_ERR_UNSUPPORTED;
-  }
-  if (cfgs[0].equilibrium == LB_EQ_POLY2) {
-    g_create_error = "the batch kernels implement the product-form equilibrium only";
-    return LB_ERR_UNSUPPORTED;
-  }
-  if (!dev_buf || ((uintptr_t)dev_buf % kAlign) != 0) {
-    g_create_error = "dev_buf must be a non-NULL 256-byte aligned device pointer";
-    return LB_ERR_INVALID_ARG;
-  }
-  if (bytes < L.total) {
-    char buf[160];
-    snprintf(buf, sizeof buf, "buffer of %zu bytes is smaller than the %zu bytes required", bytes,
-             L.total);
-    g_create_error = buf;
-    return LB_ERR_OOM;
-  }
-  lb_status s = check_device(&why);
-  if (s != LB_OK) {
-    g_create_error = why;
-    return s;
-  }
-  lb_batch* b = new lb_batch();
-  char* base = (char*)dev_buf;
-  b->nbox = nbox;
-  b->base_cfg = cfgs[0];
-  b->stream = (cudaStream_t)stream;
-  b->d_boxes = (kbc::BoxDesc*)(base + L.boxes);
-  b->d_items = (kbc::WorkItem*)(base + L.items);
-  b->max_items = L.max_items;
-  b->packed = cfgs[0].storage != LB_F64;
-  if (b->packed) b->threads = 128;
-  cudaError_t e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
-  if (e != cudaSuccess) {
-    g_create_error = std::string("creating capture stream: ") + cudaGetErrorString(e);
-    delete b;
-    return LB_ERR_CUDA;
-  }
-  std::vector<kbc::BoxDesc> descs(nbox);
-  for (int k = 0; k < nbox; ++k) {
-    lb_config c = cfgs[k];
-    c.variant = cfgs[0].variant;
-    c.gamma_mode = cfgs[0].gamma_mode;
-    c.storage = cfgs[0].storage;
-    c.scheme = cfgs[0].scheme;
-    c.equilibrium = cfgs[0].equilibrium;
-    b->cfgs.push_back(c);
-    lb_ctx* v = new lb_ctx();
-    setup_ctx(v, &c, base, L.box[k], L.shared, b->stream);
-    v->batch_view = true;
-    s = zero_state(v);
-    b->views.push_back(v);
-    kbc::BoxDesc& d = descs[k];
-    d.nx = c.nx;
-    d.ny = c.ny;
-    d.nz = c.nz;
-    d.nxy = (uint32_t)c.nx * c.ny;
-    d.pop[0] = v->box.pop[0];
-    d.pop[1] = v->box.pop[1];
-    d.gamma = v->box.gamma;
-    d.ctr = v->counters;
-    d.beta = v->box.beta;
-    d.two_beta = 2.0 * v->box.beta;
-    d.inv_beta = 1.0 / v->box.beta;
-  }
-  e = cudaMemcpyAsync(b->d_boxes, descs.data(), sizeof(kbc::BoxDesc) * nbox,
-                      cudaMemcpyHostToDevice, b->stream);
-  if (e != cudaSuccess || s != LB_OK) {
-    g_create_error = "initialising batch: " + std::string(cudaGetErrorString(e));
-    lb_batch_destroy(b);
-    return LB_ERR_CUDA;
-  }
-  s = build_items(b);
-  if (s != LB_OK) {
-    g_create_error = b->err;
-    lb_batch_destroy(b);
-    return s;
-  }
-  *out = b;
-  return LB_OK;
+  return no_throw([&]() -> lb_status {
+    if (!out) {
+      g_create_error = "out is NULL";
+      return LB_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    BatchLayout L;
+    std::string why;
+    if (!batch_layout(cfgs, nbox, &L, &why)) {
+      g_create_error = why;
+      return LB_ERR_INVALID_ARG;
+    }
+    if (cfgs[0].gamma_mode == LB_GAMMA_EXACT) {
+      g_create_error = "the batch kernels do not implement the exact stabilizer";
+      return LB_ERR_UNSUPPORTED;
+    }
+    if (cfgs[0].equilibrium == LB_EQ_POLY2) {
+      g_create_error = "the batch kernels implement the product-form equilibrium only";
+      return LB_ERR_UNSUPPORTED;
+    }
+    if (!dev_buf || ((uintptr_t)dev_buf % kAlign) != 0) {
+      g_create_error = "dev_buf must be a non-NULL 256-byte aligned device pointer";
+      return LB_ERR_INVALID_ARG;
+    }
+    if (bytes < L.total) {
+      char buf[160];
+      snprintf(buf, sizeof buf, "buffer of %zu bytes is smaller than the %zu bytes required", bytes,
+               L.total);
+      g_create_error = buf;
+      return LB_ERR_OOM;
+    }
+    lb_status s = check_device(&why);
+    if (s != LB_OK) {
+      g_create_error = why;
+      return s;
+    }
+    // owned by `guard` until the batch is complete: every early return (and a host allocation
+    // failure below) releases what was built so far
+    std::unique_ptr<lb_batch, lb_status (*)(lb_batch*)> guard(new lb_batch(), lb_batch_destroy);
+    lb_batch* b = guard.get();
+    char* base = (char*)dev_buf;
+    b->nbox = nbox;
+    b->base_cfg = cfgs[0];
+    b->stream = (cudaStream_t)stream;
+    b->d_boxes = (kbc::BoxDesc*)(base + L.boxes);
+    b->d_items = (kbc::WorkItem*)(base + L.items);
+    b->max_items = L.max_items;
+    b->packed = cfgs[0].storage != LB_F64;
+    if (b->packed) b->threads = 128;
+    cudaError_t e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      g_create_error = std::string("creating capture stream: ") + cudaGetErrorString(e);
+      return LB_ERR_CUDA;
+    }
+    std::vector<kbc::BoxDesc> descs(nbox);
+    b->cfgs.reserve(nbox);
+    b->views.reserve(nbox);
+    for (int k = 0; k < nbox; ++k) {
+      lb_config c = cfgs[k];
+      c.variant = cfgs[0].variant;
+      c.gamma_mode = cfgs[0].gamma_mode;
+      c.storage = cfgs[0].storage;
+      c.scheme = cfgs[0].scheme;
+      c.equilibrium = cfgs[0].equilibrium;
+      b->cfgs.push_back(c);
+      b->views.push_back(new lb_ctx());
+      lb_ctx* v = b->views.back();
+      setup_ctx(v, &c, base, L.box[k], L.shared, b->stream);
+      v->batch_view = true;
+      s = zero_state(v);
+      if (s != LB_OK) {
+        g_create_error = "initialising box " + std::to_string(k) + ": " + v->err;
+        return s;
+      }
+      kbc::BoxDesc& d = descs[k];
+      d.nx = c.nx;
+      d.ny = c.ny;
+      d.nz = c.nz;
+      d.nxy = (uint32_t)c.nx * c.ny;
+      d.pop[0] = v->box.pop[0];
+      d.pop[1] = v->box.pop[1];
+      d.gamma = v->box.gamma;
+      d.ctr = v->counters;
+      d.beta = v->box.beta;
+      d.two_beta = 2.0 * v->box.beta;
+      d.inv_beta = 1.0 / v->box.beta;
+    }
+    e = cudaMemcpyAsync(b->d_boxes, descs.data(), sizeof(kbc::BoxDesc) * nbox,
+                        cudaMemcpyHostToDevice, b->stream);
+    if (e != cudaSuccess) {
+      g_create_error = "uploading box descriptors: " + std::string(cudaGetErrorString(e));
+      return LB_ERR_CUDA;
+    }
+    s = build_items(b);
+    if (s != LB_OK) {
+      g_create_error = b->err;
+      return s;
+    }
+    guard.release();
+    *out = b;
+    return LB_OK;
+  });
 }
 
 lb_status lb_batch_destroy(lb_batch* b) {
@@ -1032,159 +1107,151 @@ lb_ctx* lb_batch_box(lb_batch* b, int32_t box) {
 }
 
 lb_status lb_batch_step(lb_batch* b, int64_t n) {
-  Range range_("lb_batch_step");
-  if (!b) return LB_ERR_INVALID_ARG;
-  if (n < 0) return bfail(b, LB_ERR_INVALID_ARG, "n must be >= 0");
-  if (n == 0) return LB_OK;
-  // all boxes must share one time (initialising a box resets its t to 0)
-  for (lb_ctx* v : b->views)
-    if (v->t != b->views[0]->t)
-      return bfail(b, LB_ERR_INVALID_ARG, "boxes of a batch are at different times; step, "
-                                          "initialise or re-time all of them together");
-  b->t = b->views[0]->t;
-  const auto key = std::make_pair(n, (int)(b->t & 1));
-  auto it = b->graphs.find(key);
-  if (it == b->graphs.end()) {
-    cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess)
-      return bfail(b, LB_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
-    cudaError_t le = cudaSuccess;
-    for (int64_t k = 0; k < n; ++k) {
-      const bool record = (k == n - 1);
-      if (record) {
-        for (lb_ctx* v : b->views)
-          if (le == cudaSuccess)
-            le = cudaMemsetAsync(&v->counters->guarded, 0, sizeof(unsigned long long),
-                                 b->capture_stream);
+  return no_throw([&]() -> lb_status {
+    Range range_("lb_batch_step");
+    if (!b) return LB_ERR_INVALID_ARG;
+    if (n < 0) return bfail(b, LB_ERR_INVALID_ARG, "n must be >= 0");
+    if (n == 0) return LB_OK;
+    // all boxes must share one time (initialising a box resets its t to 0)
+    for (lb_ctx* v : b->views)
+      if (v->t != b->views[0]->t)
+        return bfail(b, LB_ERR_INVALID_ARG, "boxes of a batch are at different times; step, "
+                                            "initialise or re-time all of them together");
+    b->t = b->views[0]->t;
+    // replay graphs of at most kGraphSteps steps, so that the cache stays bounded (one graph of
+    // kGraphSteps steps and one tail per length, per parity) whatever n the caller passes
+    lb_status st = LB_OK;
+    for (int64_t done = 0; done < n && st == LB_OK;) {
+      const int64_t len = (n - done > kGraphSteps) ? kGraphSteps : n - done;
+      const bool record = (done + len == n);
+      cudaGraphExec_t exec = nullptr;
+      st = batch_graph(b, len, record, &exec);
+      if (st != LB_OK) break;
+      cudaError_t e = cudaGraphLaunch(exec, b->stream);
+      if (e != cudaSuccess) {
+        st = bfail(b, LB_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+        break;
       }
-      if (le == cudaSuccess) le = enqueue_batch_step(b, b->t + k, record, b->capture_stream);
+      b->t += len;
+      done += len;
     }
-    e = cudaStreamEndCapture(b->capture_stream, &graph);
-    if (le != cudaSuccess || e != cudaSuccess) {
-      if (graph) cudaGraphDestroy(graph);
-      return bfail(b, LB_ERR_CUDA, std::string("capturing batch steps: ") +
-                                       cudaGetErrorString(le != cudaSuccess ? le : e));
+    for (lb_ctx* v : b->views) {
+      v->t = b->t;
+      v->gamma_valid = (st == LB_OK);
     }
-    cudaGraphExec_t exec = nullptr;
-    e = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess)
-      return bfail(b, LB_ERR_CUDA, std::string("instantiating graph: ") + cudaGetErrorString(e));
-    it = b->graphs.emplace(key, exec).first;
-  }
-  cudaError_t e = cudaGraphLaunch(it->second, b->stream);
-  if (e != cudaSuccess)
-    return bfail(b, LB_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
-  b->t += n;
-  for (lb_ctx* v : b->views) {
-    v->t = b->t;
-    v->gamma_valid = true;
-  }
-  return LB_OK;
+    return st;
+  });
 }
 
 lb_status lb_batch_diagnostics(lb_batch* b, lb_diag* out) {
-  if (!b || !out) return b ? bfail(b, LB_ERR_INVALID_ARG, "out is NULL") : LB_ERR_INVALID_ARG;
-  lb_status worst = LB_OK;
-  for (int k = 0; k < b->nbox; ++k) {
-    lb_status s = lb_diagnostics(b->views[k], &out[k]);
-    if (s == LB_ERR_NONFINITE) {
-      worst = s;
-      b->err = "box " + std::to_string(k) + ": " + b->views[k]->err;
-    } else if (s != LB_OK) {
-      b->err = "box " + std::to_string(k) + ": " + b->views[k]->err;
-      return s;
+  return no_throw([&]() -> lb_status {
+    if (!b || !out) return b ? bfail(b, LB_ERR_INVALID_ARG, "out is NULL") : LB_ERR_INVALID_ARG;
+    lb_status worst = LB_OK;
+    for (int k = 0; k < b->nbox; ++k) {
+      lb_status s = lb_diagnostics(b->views[k], &out[k]);
+      if (s == LB_ERR_NONFINITE) {
+        worst = s;
+        b->err = "box " + std::to_string(k) + ": " + b->views[k]->err;
+      } else if (s != LB_OK) {
+        b->err = "box " + std::to_string(k) + ": " + b->views[k]->err;
+        return s;
+      }
     }
-  }
-  return worst;
+    return worst;
+  });
 }
 
 lb_status lb_batch_set_kernel(lb_batch* b, int32_t kind) {
-  if (!b) return LB_ERR_INVALID_ARG;
-  if (kind != LB_KERNEL_AUTO && kind != LB_KERNEL_DIRECT && kind != LB_KERNEL_PACKED)
-    return bfail(b, LB_ERR_INVALID_ARG, "batch kernel must be LB_KERNEL_AUTO, _DIRECT or _PACKED");
-  const bool fp32 = b->base_cfg.storage != LB_F64;
-  if (kind == LB_KERNEL_PACKED && !fp32)
-    return bfail(b, LB_ERR_UNSUPPORTED, "the packed kernel needs FP32 arithmetic");
-  b->packed = fp32 && kind != LB_KERNEL_DIRECT;
-  b->threads = b->packed ? 128 : 256;
-  return build_items(b);
+  return no_throw([&]() -> lb_status {
+    if (!b) return LB_ERR_INVALID_ARG;
+    if (kind != LB_KERNEL_AUTO && kind != LB_KERNEL_DIRECT && kind != LB_KERNEL_PACKED)
+      return bfail(b, LB_ERR_INVALID_ARG, "batch kernel must be LB_KERNEL_AUTO, _DIRECT or _PACKED");
+    const bool fp32 = b->base_cfg.storage != LB_F64;
+    if (kind == LB_KERNEL_PACKED && !fp32)
+      return bfail(b, LB_ERR_UNSUPPORTED, "the packed kernel needs FP32 arithmetic");
+    b->packed = fp32 && kind != LB_KERNEL_DIRECT;
+    b->threads = b->packed ? 128 : 256;
+    return build_items(b);
+  });
 }
 
 lb_status lb_batch_set_tile(lb_batch* b, int32_t threads, int32_t tile) {
-  if (!b) return LB_ERR_INVALID_ARG;
-  const int maxt = b->base_cfg.storage == LB_F64 ? 256 : 512;
-  if (b->packed && threads != 128)
-    return bfail(b, LB_ERR_INVALID_ARG, "the packed batch kernel runs 128 threads per block");
-  if (threads < 32 || threads > maxt || threads % 32 != 0 || tile < 32)
-    return bfail(b, LB_ERR_INVALID_ARG, "threads must be a multiple of 32 in [32, 512] (256 for "
-                                        "FP64); tile >= 32");
-  b->threads = threads;
-  b->tile = tile;
-  return build_items(b);
+  return no_throw([&]() -> lb_status {
+    if (!b) return LB_ERR_INVALID_ARG;
+    const int maxt = b->base_cfg.storage == LB_F64 ? 256 : 512;
+    if (b->packed && threads != 128)
+      return bfail(b, LB_ERR_INVALID_ARG, "the packed batch kernel runs 128 threads per block");
+    if (threads < 32 || threads > maxt || threads % 32 != 0 || tile < 32)
+      return bfail(b, LB_ERR_INVALID_ARG, "threads must be a multiple of 32 in [32, 512] (256 for "
+                                          "FP64); tile >= 32");
+    b->threads = threads;
+    b->tile = tile;
+    return build_items(b);
+  });
 }
 
 lb_status lb_batch_autotune(lb_batch* b, int32_t trial_steps, int32_t* best_threads,
                             int32_t* best_tile, double* best_ms) {
-  if (!b) return LB_ERR_INVALID_ARG;
-  if (trial_steps < 1) return bfail(b, LB_ERR_INVALID_ARG, "trial_steps must be >= 1");
-  const int cand_threads[] = {128, 256, 512};
-  const int maxt = b->base_cfg.storage == LB_F64 ? 256 : 512;
-  const int cand_tile[] = {256, 512, 1024, 2048, 4096};
-  cudaEvent_t e0, e1;
-  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
-    return bfail(b, LB_ERR_CUDA, "creating timing events");
-  double best = 1e300;
-  int bt = b->threads, bl = b->tile;
-  b->t = b->views[0]->t;
-  lb_status st = LB_OK;
-  for (int th : cand_threads) {
-    if (th > maxt || (b->packed && th != 128)) continue;
-    for (int tl : cand_tile) {
-      b->threads = th;
-      b->tile = tl;
-      st = build_items(b);
-      if (st != LB_OK) break;
-      cudaError_t e = enqueue_batch_step(b, b->t, false, b->stream);  // warm-up
-      b->t += 1;
-      if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
-      for (int k = 0; k < trial_steps && e == cudaSuccess; ++k) {
-        e = enqueue_batch_step(b, b->t, false, b->stream);
+  return no_throw([&]() -> lb_status {
+    if (!b) return LB_ERR_INVALID_ARG;
+    if (trial_steps < 1) return bfail(b, LB_ERR_INVALID_ARG, "trial_steps must be >= 1");
+    const int cand_threads[] = {128, 256, 512};
+    const int maxt = b->base_cfg.storage == LB_F64 ? 256 : 512;
+    const int cand_tile[] = {256, 512, 1024, 2048, 4096};
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+      return bfail(b, LB_ERR_CUDA, "creating timing events");
+    double best = 1e300;
+    int bt = b->threads, bl = b->tile;
+    b->t = b->views[0]->t;
+    lb_status st = LB_OK;
+    for (int th : cand_threads) {
+      if (th > maxt || (b->packed && th != 128)) continue;
+      for (int tl : cand_tile) {
+        b->threads = th;
+        b->tile = tl;
+        st = build_items(b);
+        if (st != LB_OK) break;
+        cudaError_t e = enqueue_batch_step(b, b->t, false, b->stream);  // warm-up
         b->t += 1;
+        if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+        for (int k = 0; k < trial_steps && e == cudaSuccess; ++k) {
+          e = enqueue_batch_step(b, b->t, false, b->stream);
+          b->t += 1;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+          st = bfail(b, LB_ERR_CUDA, std::string("autotune trial: ") + cudaGetErrorString(e));
+          break;
+        }
+        const double per = ms / trial_steps;
+        if (per < best) {
+          best = per;
+          bt = th;
+          bl = tl;
+        }
       }
-      if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
-      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-      float ms = 0.f;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-      if (e != cudaSuccess) {
-        st = bfail(b, LB_ERR_CUDA, std::string("autotune trial: ") + cudaGetErrorString(e));
-        break;
-      }
-      const double per = ms / trial_steps;
-      if (per < best) {
-        best = per;
-        bt = th;
-        bl = tl;
-      }
+      if (st != LB_OK) break;
     }
-    if (st != LB_OK) break;
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  for (lb_ctx* v : b->views) {
-    v->t = b->t;
-    v->gamma_valid = false;
-  }
-  if (st != LB_OK) return st;
-  b->threads = bt;
-  b->tile = bl;
-  st = build_items(b);
-  if (st != LB_OK) return st;
-  if (best_threads) *best_threads = bt;
-  if (best_tile) *best_tile = bl;
-  if (best_ms) *best_ms = best;
-  return LB_OK;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (lb_ctx* v : b->views) {
+      v->t = b->t;
+      v->gamma_valid = false;
+    }
+    if (st != LB_OK) return st;
+    b->threads = bt;
+    b->tile = bl;
+    st = build_items(b);
+    if (st != LB_OK) return st;
+    if (best_threads) *best_threads = bt;
+    if (best_tile) *best_tile = bl;
+    if (best_ms) *best_ms = best;
+    return LB_OK;
+  });
 }
 
 }  // extern "C"

@@ -525,6 +525,37 @@ def test_batch_autotune_and_graph_replay(kbc):
     assert np.array_equal(got, ref.get_populations())
 
 
+
+def test_batch_step_longer_than_one_graph(kbc):
+    """lb_batch_step splits n into graphs of at most 64 steps; 131 + 1 steps (chunks 64, 64, 3,
+    then one step from odd parity) of an AA batch equal 132 single-box steps bitwise, and
+    gamma is recorded on the last step only."""
+    boxes = [{"n": 12, "nu": 2e-3}, {"n": 16, "nu": 5e-4}]
+    batch = lb.Batch(boxes, storage="f32", scheme="aa")
+    fields = []
+    for k, b in enumerate(boxes):
+        rho, u = workloads.taylor_green(b["n"], 0.04)
+        fields.append((rho, u))
+        lb.lb_init_field(batch.box(k), rho.ctypes.data, np.ascontiguousarray(u).ctypes.data,
+                         False)
+    batch.step(131)
+    batch.step(1)
+    diags = batch.diagnostics()
+    for k, b in enumerate(boxes):
+        ref = lb.Lattice(b["n"], nu=b["nu"], storage="f32", scheme="aa")
+        ref.set_kernel("packed")
+        ref.init_field(*fields[k])
+        ref.step(132)
+        got = np.empty((27, b["n"] ** 3))
+        lb.lb_get_populations(batch.box(k), got.ctypes.data, False)
+        assert np.array_equal(got, ref.get_populations().reshape(27, -1))
+        d = ref.diagnostics()
+        assert diags[k]["step"] == 132
+        assert diags[k]["gamma_mean"] == d["gamma_mean"]
+        assert diags[k]["den_guard_count"] == d["den_guard_count"]
+        ref.close()
+
+
 # ------------------------------------------------------------------ full-size sampled parity
 
 def _sampled_step_check(lat, nsample, tol, rng, half=False):
