@@ -87,12 +87,17 @@ NCU_TRAFFIC_PER_LUP = {
 
 
 def parse_workload(name):
-    """hit<N>_<storage>_<scheme> (random spectrum, k0=4, u_rms=0.04, nu=2e-4) or
-    kida<N>_<storage>_<scheme> (U0=0.05, nu=5e-5), e.g. hit128_f32_pull."""
+    """hit<N>_<storage>_<scheme> (random spectrum, k0=4, u_rms=0.04, nu=2e-4),
+    kida<N>_<storage>_<scheme> (U0=0.05, nu=5e-5), e.g. hit128_f32_pull, or (as a variant only)
+    batch<K>_<storage>_<scheme>, the first K boxes of the uneven ensemble."""
     for v in [MAIN] + VARIANTS:
         if v["name"] == name:
             return dict(v)
     import re
+    m = re.fullmatch(r"batch(\d+)_(f64|f32|f16)_(pull|aa)", name)
+    if m:
+        return {"name": name, "field": "batch", "nbox": int(m.group(1)), "storage": m.group(2),
+                "scheme": m.group(3), "steps": 200}
     m = re.fullmatch(r"(hit|kida)(\d+)_(f64|f32|f16)_(pull|aa)", name)
     if not m:
         raise SystemExit("unknown workload %r" % name)
@@ -410,11 +415,13 @@ def roofline(storage, mlups, peak, peak_kind, traffic=None):
 # ---------------------------------------------------------------- arms
 
 def main_ours(args, rank, world, local):
+    w = parse_workload(args.workload)
+    if w["field"] == "batch":
+        raise SystemExit("a batch workload runs as a variant: --variants %s" % w["name"])
     import torch
     torch.cuda.set_device(local)
     from paper_1507_02518_gb300 import lb
     lb.load()
-    w = parse_workload(args.workload)
     peak, peak_kind = hbm_peak()
     # warm-up and timed region (max over ranks)
     barrier(world)
@@ -446,7 +453,9 @@ def main_ours(args, rank, world, local):
     clk_mhz = clk.summary().get("sm_mhz")
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     if not args.no_variants:
-        for v in VARIANTS:
+        chosen = VARIANTS if args.variants is None else [
+            parse_workload(name) for name in args.variants.split(",") if name]
+        for v in chosen:
             try:
                 vs = v.get("steps", 200)
                 if v["field"] == "batch":
@@ -560,6 +569,9 @@ def parse_args(argv=None):
     p.add_argument("--workload", default=MAIN["name"],
                    help="hit<N>_<f64|f32|f16>_<pull|aa> or kida<N>_..., default %s" % MAIN["name"])
     p.add_argument("--no-variants", action="store_true")
+    p.add_argument("--variants", default=None,
+                   help="comma-separated workloads to run as variants instead of the default "
+                        "list (names as for --workload, or batch<K>_<storage>_<scheme>)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     a = p.parse_args(argv)

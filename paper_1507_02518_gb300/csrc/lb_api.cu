@@ -759,8 +759,10 @@ lb_status lb_set_wait_budget(lb_ctx* c, uint64_t cycles, int32_t stall_copies) {
 
 lb_status lb_set_block(lb_ctx* c, int32_t bx, int32_t by) {
   if (!c) return LB_ERR_INVALID_ARG;
+  if (bx < 32 || bx > 512 || bx % 32 != 0 || by < 1 || by > 16)
+    return fail(c, LB_ERR_INVALID_ARG, "block must be bx*by in {64,128,256,512}, bx % 32 == 0");
   const int n = bx * by;
-  if (bx < 32 || bx % 32 != 0 || by < 1 || (n != 64 && n != 128 && n != 256 && n != 512))
+  if (n != 64 && n != 128 && n != 256 && n != 512)
     return fail(c, LB_ERR_INVALID_ARG, "block must be bx*by in {64,128,256,512}, bx % 32 == 0");
   if (c->cfg.storage == LB_F64 && n > 256)
     return fail(c, LB_ERR_INVALID_ARG, "FP64 storage allows at most 256 threads per block");

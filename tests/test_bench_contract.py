@@ -24,3 +24,20 @@ def test_reference_arm_prints_one_json_line():
     assert d["steps"] == 3 and d["warmup"] == 3
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_workload_names_parse():
+    sys.path.insert(0, ROOT)
+    import bench
+    import pytest
+    w = bench.parse_workload("batch16_f32_aa")
+    assert (w["field"], w["nbox"], w["storage"], w["scheme"]) == ("batch", 16, "f32", "aa")
+    w = bench.parse_workload("hit64_f16_pull")
+    assert (w["field"], w["n"], w["storage"], w["scheme"]) == ("spectrum", 64, "f16", "pull")
+    assert bench.parse_workload("kida100_f64_aa")["field"] == "kida"
+    for v in [bench.MAIN] + bench.VARIANTS:
+        assert bench.parse_workload(v["name"]) == v
+    with pytest.raises(SystemExit):
+        bench.parse_workload("hit64_bf16_pull")
+    a = bench.parse_args(["--variants", "batch16_f32_pull,hit64_f32_aa"])
+    assert a.variants == "batch16_f32_pull,hit64_f32_aa" and a.warmup >= 3
