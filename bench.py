@@ -346,7 +346,8 @@ def run_e2e(w, steps):
     rho, u, rho_out, u_out = rho_t.numpy(), u_t.numpy(), rho_o.numpy(), u_o.numpy()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    lat.init_field(rho, u)
+    lat.init_field(rho, u)                        # returns after its copies and kernels
+    t1 = time.perf_counter()
     every = w.get("diag_every", 0) or steps
     k = 0
     while k < steps:
@@ -355,13 +356,19 @@ def run_e2e(w, steps):
         k += c
         if w.get("diag_every"):
             lat.diagnostics()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
     lb.lb_moments(lat.ctx, rho_out.ctypes.data, u_out.ctypes.data, False)
     torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
+    t3 = time.perf_counter()
+    dt = t3 - t0
     h2d = rho.nbytes + u.nbytes
     d2h = rho_out.nbytes + u_out.nbytes + (steps // every) * (16 * 8 + 8)
     return {"value": lat.P * steps / dt / 1e6, "unit": "MLUPS",
-            "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps}
+            "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps,
+            "phase_ms": {"h2d_and_init": round(1e3 * (t1 - t0), 2),
+                         "steps_and_diagnostics": round(1e3 * (t2 - t1), 2),
+                         "moments_and_d2h": round(1e3 * (t3 - t2), 2)}}
 
 
 def cpu_baseline(w, budget_s=12.0):
