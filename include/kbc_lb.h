@@ -18,7 +18,10 @@
  *   memory       the library allocates no device memory. The caller passes one device buffer
  *                of at least lb_required_bytes() bytes and keeps it alive until lb_destroy;
  *                the library never frees it. "on_device" arguments say whether a pointer is
- *                device (1) or host (0) memory; host pointers may be pageable.
+ *                device (1) or host (0) memory. Host memory may be pageable (copied through
+ *                the staging area in chunks) or page-locked (cudaHostAlloc, cudaHostRegister:
+ *                the kernels read or write it in place over the host-device link, no
+ *                staging copies); either way the call has finished with it on return.
  *   streams      all work is enqueued on the CUDA stream given to lb_create (NULL = legacy
  *                default stream). lb_step never synchronises; lb_moments, lb_diagnostics,
  *                lb_get_populations and lb_set_populations synchronise the stream.
@@ -143,7 +146,8 @@ const char *lb_last_error(const lb_ctx *ctx);
 
 /* Set f(x, 0) = f_eq(rho(x), u(x)) by eq:entropic_eq and t = 0.
  *   rho  FP64 [P] (NULL: rho = 1 everywhere);  u  FP64 [3][P] (u_x plane, u_y, u_z).
- * Host inputs are copied through the staging area in chunks; |u_a| < 1 is required. */
+ * Pageable host inputs are copied through the staging area in chunks, page-locked ones are
+ * read in place; |u_a| < 1 is required. Host inputs: synchronises. */
 lb_status lb_init_field(lb_ctx *ctx, const double *rho, const double *u, int on_device);
 
 /* Consistent initial state (Sec. "Numerical Simulations": the initial density and higher
@@ -155,7 +159,8 @@ lb_status lb_init_field(lb_ctx *ctx, const double *rho, const double *u, int on_
  * is measured, on rho - 1 rounded to FP32; the loop stops when it is <= tol (a negative tol
  * runs max_iters) or after max_iters iterations, rounded up to an even count. The result is
  * the state at t = 0; lb_diagnostics has no gamma until the next lb_step.
- *   u0            FP64 [3][P], host (copied in chunks) or device (on_device != 0)
+ *   u0            FP64 [3][P], host (pageable: copied in chunks; page-locked: read in
+ *                 place) or device (on_device != 0)
  *   nu_pre        > 0, the pre-solve's own relaxation (1/6 relaxes fully to f_eq each
  *                 iteration)
  *   from_current  nonzero: start from the current state instead of f_eq(1, u0), e.g. from

@@ -163,6 +163,19 @@ lb_status check_device(std::string* why) {
   return LB_OK;
 }
 
+// The device address of a host pointer into page-locked memory (cudaHostAlloc, or registered
+// with cudaHostRegister), which kernels can read and write directly over the host-device link;
+// NULL for pageable memory or when the platform maps no such address.
+const void* mapped_host(const void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return (a.type == cudaMemoryTypeHost) ? a.devicePointer : nullptr;
+}
+
 }  // namespace
 
 void kbc_set_thread_error(const std::string& msg) { g_create_error = msg; }
@@ -371,6 +384,13 @@ lb_status lb_init_field(lb_ctx* c, const double* rho, const double* u, int on_de
     if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
     return LB_OK;
   }
+  const double* mu = (const double*)mapped_host(u);
+  const double* mrho = (const double*)mapped_host(rho);
+  if (mu && (!rho || mrho)) {  // page-locked inputs: the kernel reads them in place
+    e = dispatch(c, [&](auto ops) { return ops.init(c->box, 0, mrho, mu, 0, P, P, c->stream); });
+    if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
+    return sync(c, "init");
+  }
   for (uint64_t n0 = 0; n0 < P; n0 += c->stage_nodes) {
     const uint64_t cnt = (P - n0 < c->stage_nodes) ? P - n0 : c->stage_nodes;
     double* srho = c->staging;
@@ -407,6 +427,10 @@ lb_status lb_presolve(lb_ctx* c, const double* u0, int on_device, double nu_pre,
   cudaError_t e = cudaSuccess;
   // u0 into the diagnostics velocity field (collision precision); unless continuing from the
   // current state, f = f_eq(1, u0) at t = 0
+  if (!on_device && mapped_host(u0)) {  // page-locked input: read in place
+    u0 = (const double*)mapped_host(u0);
+    on_device = 1;
+  }
   if (on_device) {
     e = dispatch(c, [&](auto ops) { return ops.convert_u(u0, c->ufield, 0, P, P, P, c->stream); });
     if (e == cudaSuccess && !from_current)
@@ -473,6 +497,10 @@ lb_status lb_presolve(lb_ctx* c, const double* u0, int on_device, double nu_pre,
     }
     if (res <= tol) break;
   }
+  if (done == 0) {  // no iteration ran: the set-up kernels still read u0
+    lb_status st = sync(c, "pre-solve set-up");
+    if (st != LB_OK) return st;
+  }
   c->t = 0;
   if (iters) *iters = done;
   if (residual) *residual = res;
@@ -504,6 +532,15 @@ lb_status lb_moments(lb_ctx* c, double* rho, double* u, int on_device) {
   if (!u) return fail(c, LB_ERR_INVALID_ARG, "u is NULL");
   const uint64_t P = c->box.P;
   cudaError_t e;
+  if (!on_device) {  // page-locked outputs: the kernel writes them in place
+    double* mu = (double*)mapped_host(u);
+    double* mrho = (double*)mapped_host(rho);
+    if (mu && (!rho || mrho)) {
+      rho = mrho;
+      u = mu;
+      on_device = 1;
+    }
+  }
   if (on_device) {
     e = dispatch(c, [&](auto ops) { return ops.moments(c->box, c->t, rho, u, 0, P, P, c->stream); });
     if (e != cudaSuccess) return cuda_fail(c, e, "moments kernel");
@@ -658,6 +695,10 @@ lb_status lb_get_populations(lb_ctx* c, double* f, int on_device) {
   if (!f) return fail(c, LB_ERR_INVALID_ARG, "f is NULL");
   const uint64_t P = c->box.P;
   cudaError_t e;
+  if (!on_device && mapped_host(f)) {  // page-locked output: written in place
+    f = (double*)mapped_host(f);
+    on_device = 1;
+  }
   if (on_device) {
     e = dispatch(c, [&](auto ops) { return ops.get(c->box, c->t, f, 0, P, P, c->stream); });
     if (e != cudaSuccess) return cuda_fail(c, e, "export kernel");
@@ -682,6 +723,10 @@ lb_status lb_set_populations(lb_ctx* c, const double* f, int on_device) {
   const uint64_t P = c->box.P;
   c->gamma_valid = false;
   cudaError_t e;
+  if (!on_device && mapped_host(f)) {  // page-locked input: read in place
+    f = (const double*)mapped_host(f);
+    on_device = 1;
+  }
   if (on_device) {
     e = dispatch(c, [&](auto ops) { return ops.set(c->box, c->t, f, 0, P, P, c->stream); });
     if (e != cudaSuccess) return cuda_fail(c, e, "import kernel");
