@@ -29,27 +29,31 @@ __global__ void __launch_bounds__(MaxThreads<S>::value) step_kernel(const S* src
   node_update<S, MODE, RECORD, CENTRAL, EXACT, POLY>(src, dst, g, x, y, z, cp, gamma_out, ctr);
 }
 
-// Two nodes per thread with packed FP32x2 arithmetic: a block of 128 threads covers 256
-// consecutive x nodes of one row, each warp 64 of them as (x, x + 32) pairs.
+// Two nodes per thread with packed FP32x2 arithmetic: a block of up to 128 threads covers
+// 2 x blockDim.x consecutive x nodes of one row, each warp 64 of them as (x, x + 32) pairs.
 template <typename S, int MODE, bool RECORD, bool CENTRAL, bool POLY = false>
 __global__ void __launch_bounds__(128, 3) pair_step_kernel(const S* src, S* dst, Geo g,
                                                         CollideParams cp, float* gamma_out,
                                                         StepCounters* ctr) {
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t xa = blockIdx.x * 256 + warp * 64 + lane;
+  const uint32_t xa = blockIdx.x * (2 * blockDim.x) + warp * 64 + lane;
   const uint32_t xb = xa + 32;
   if (xa >= g.nx) return;
   node_update2<S, MODE, RECORD, CENTRAL, POLY>(src, dst, g, xa, xb, xb < g.nx, blockIdx.y,
                                                blockIdx.z, cp, gamma_out, ctr);
 }
 
-// one block per 256-node row segment (a persistent grid measured slower on GB300)
+// Blocks of whole row segments (a persistent grid measured slower on GB300): a row takes
+// ceil(nx / 256) blocks, each of as few warps (<= 4, 64 nodes each) as cover its share, so
+// that rows of 128 nodes or fewer leave no warp of the block without nodes.
 template <typename S, int MODE, bool RECORD, bool CENTRAL, bool POLY = false>
 static cudaError_t launch_pair(const S* src, S* dst, const Geo& g, const CollideParams& cp,
                                float* gamma_out, StepCounters* ctr, cudaStream_t st) {
-  const dim3 grid((g.nx + 255) / 256, g.ny, g.nz);
-  pair_step_kernel<S, MODE, RECORD, CENTRAL, POLY><<<grid, 128, 0, st>>>(src, dst, g, cp,
-                                                                         gamma_out, ctr);
+  const uint32_t blocks_per_row = (g.nx + 255) / 256;
+  const uint32_t warps = (g.nx + 64 * blocks_per_row - 1) / (64 * blocks_per_row);  // 1..4
+  const dim3 grid((g.nx + 64 * warps - 1) / (64 * warps), g.ny, g.nz);
+  pair_step_kernel<S, MODE, RECORD, CENTRAL, POLY><<<grid, 32 * warps, 0, st>>>(
+      src, dst, g, cp, gamma_out, ctr);
   return cudaGetLastError();
 }
 
