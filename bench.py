@@ -76,13 +76,9 @@ FP64_PIPE_PER_SM_PER_CYCLE = 2.0
 # capture, keyed by a hash of the kernel sources; a changed kernel gets no traffic figure until
 # it is profiled again.
 NCU_TRAFFIC_PER_LUP = {
-    # pair_step_kernel<float, MODE_PULL> on 128^3: 226.59 MB read + 178.89 MB written
-    # for 2,097,152 nodes (profiles/pair_step_kernel_f32_pull_hit128.md)
-    "d5665b707ce5683e": 405.11e6 / 2097152,
-    "14000bf9f1c1af59": 405.12e6 / 2097152,
-    "40c56e8d5b2ff503": 405.52e6 / 2097152,
-    "0193b9258dd95b6c": 405.46e6 / 2097152,
-    "ea6c3acf56bd2b3e": 405.47e6 / 2097152,
+    # pair_step_kernel<float, MODE_PULL>, the bench's own launch on 256^3: 1812.17 MB read +
+    # 1757.26 MB written for 16,777,216 nodes (profiles/pair_step_kernel_f32_pull_hit256.md)
+    "ed2315303763a9a1": 3569.43e6 / 16777216,
 }
 
 
