@@ -43,14 +43,28 @@ __global__ void __launch_bounds__(128, 3) pair_step_kernel(const S* src, S* dst,
                                                blockIdx.z, cp, gamma_out, ctr);
 }
 
-// Blocks of whole row segments (a persistent grid measured slower on GB300): a row takes
-// ceil(nx / 256) blocks, each of as few warps (<= 4, 64 nodes each) as cover its share, so
-// that rows of 128 nodes or fewer leave no warp of the block without nodes.
+// Warps per block of the pair kernel: a row needs ceil(nx / 64) warps; blocks of w <= 4 warps
+// launch ceil(rows' warps / w) w warps per row, so take the w with the fewest warps left
+// without nodes (the larger w on a tie): nx = 100 -> 2, 256 -> 4, 400 -> 1, 600 -> 2.
+inline uint32_t pair_block_warps(uint32_t nx) {
+  const uint32_t need = (nx + 63) / 64;
+  uint32_t best = 4, best_idle = (need + 3) / 4 * 4 - need;
+  for (uint32_t w = 3; w >= 1; --w) {
+    const uint32_t idle = (need + w - 1) / w * w - need;
+    if (idle < best_idle) {
+      best = w;
+      best_idle = idle;
+    }
+  }
+  return best;
+}
+
+// Blocks of whole row segments (a persistent grid measured slower on GB300), sized by
+// pair_block_warps.
 template <typename S, int MODE, bool RECORD, bool CENTRAL, bool POLY = false>
 static cudaError_t launch_pair(const S* src, S* dst, const Geo& g, const CollideParams& cp,
                                float* gamma_out, StepCounters* ctr, cudaStream_t st) {
-  const uint32_t blocks_per_row = (g.nx + 255) / 256;
-  const uint32_t warps = (g.nx + 64 * blocks_per_row - 1) / (64 * blocks_per_row);  // 1..4
+  const uint32_t warps = pair_block_warps(g.nx);
   const dim3 grid((g.nx + 64 * warps - 1) / (64 * warps), g.ny, g.nz);
   pair_step_kernel<S, MODE, RECORD, CENTRAL, POLY><<<grid, 32 * warps, 0, st>>>(
       src, dst, g, cp, gamma_out, ctr);
