@@ -781,21 +781,29 @@ __device__ __forceinline__ void node_update(const S* src, S* dst, const Geo& g, 
   }
 }
 
-// Two nodes of one row per thread, (xa, xb) = (x, x + 32) so every load and store instruction
-// of a warp stays coalesced; the collision runs once on float2 lanes with packed FP32x2
-// instructions. When xb is outside the box (vb false) lane 1 recomputes node xa and is not
-// stored. FP32 arithmetic only (S = float or uint16_t).
-template <typename S, int MODE, bool RECORD, bool CENTRAL = false, bool POLY = false>
+// Two nodes per thread, a = (xa, ya, za) and b = (xb, yb, zb), laid out so that every load
+// and store instruction of a warp stays coalesced (b = a + 32 in the node order); the
+// collision runs once on float2 lanes with packed FP32x2 instructions. When b is outside the
+// box or the work unit (vb false) the caller passes b = a: lane 1 recomputes node a and is
+// not stored. SAME_ROW: b lies in a's row (yb = ya, zb = za), which keeps fewer coordinates
+// live. FP32 arithmetic only (S = float or uint16_t).
+template <typename S, int MODE, bool RECORD, bool CENTRAL = false, bool POLY = false,
+          bool SAME_ROW = true>
 __device__ __forceinline__ void node_update2(const S* src, S* dst, const Geo& g, uint32_t xa,
-                                             uint32_t xb, bool vb, uint32_t y, uint32_t z,
+                                             uint32_t ya, uint32_t za, uint32_t xb,
+                                             uint32_t yb, uint32_t zb, bool vb,
                                              const CollideParams& cp, float* gamma_out,
                                              StepCounters* ctr) {
   using C = Codec<S>;
   using Pat = Pattern<MODE>;
   static_assert(std::is_same<typename C::R, float>::value, "FP32 arithmetic only");
+  if constexpr (SAME_ROW) {
+    yb = ya;
+    zb = za;
+  }
   Nbr na, nb;
-  na.init(g, xa, y, z);
-  nb.init(g, vb ? xb : xa, y, z);
+  na.init(g, xa, ya, za);
+  nb.init(g, xb, yb, zb);
   float2 d[27];
   Unroll<0, 27>::run([&](auto ic) {
     constexpr int I = decltype(ic)::value;
@@ -815,10 +823,17 @@ __device__ __forceinline__ void node_update2(const S* src, S* dst, const Geo& g,
   if constexpr (MODE != MODE_PULL) asm volatile("" : "+l"(Ps), "+l"(dsts));
   Nbr sa = na, sb = nb;
   if constexpr (MODE == MODE_AA_ODD) {
-    uint32_t xa2 = xa, xb2 = vb ? xb : xa, y2 = y, z2 = z;
-    asm volatile("" : "+r"(xa2), "+r"(xb2), "+r"(y2), "+r"(z2));
-    sa.init(g, xa2, y2, z2);
-    sb.init(g, xb2, y2, z2);
+    if constexpr (SAME_ROW) {
+      uint32_t xa2 = xa, xb2 = xb, y2 = ya, z2 = za;
+      asm volatile("" : "+r"(xa2), "+r"(xb2), "+r"(y2), "+r"(z2));
+      sa.init(g, xa2, y2, z2);
+      sb.init(g, xb2, y2, z2);
+    } else {
+      uint32_t xa2 = xa, xb2 = xb, ya2 = ya, za2 = za, yb2 = yb, zb2 = zb;
+      asm volatile("" : "+r"(xa2), "+r"(xb2), "+r"(ya2), "+r"(za2), "+r"(yb2), "+r"(zb2));
+      sa.init(g, xa2, ya2, za2);
+      sb.init(g, xb2, yb2, zb2);
+    }
   }
   Unroll<0, 27>::run([&](auto ic) {
     constexpr int I = decltype(ic)::value;

@@ -29,6 +29,23 @@ __global__ void __launch_bounds__(MaxThreads<S>::value) step_kernel(const S* src
   node_update<S, MODE, RECORD, CENTRAL, EXACT, POLY>(src, dst, g, x, y, z, cp, gamma_out, ctr);
 }
 
+// Moves node (x, y, z) of a box with rows of nx nodes and planes of ny rows k nodes forward in
+// the node order (x fastest); x may start at or beyond nx (it is reduced first).
+__device__ __forceinline__ void advance_node(uint32_t& x, uint32_t& y, uint32_t& z, uint32_t k,
+                                             uint32_t nx, uint32_t ny) {
+  x += k;
+  if (x >= nx) {
+    const uint32_t r = x / nx;
+    x -= r * nx;
+    y += r;
+    if (y >= ny) {
+      const uint32_t p = y / ny;
+      y -= p * ny;
+      z += p;
+    }
+  }
+}
+
 // Two nodes per thread with packed FP32x2 arithmetic: a block of up to 128 threads covers
 // 2 x blockDim.x consecutive x nodes of one row, each warp 64 of them as (x, x + 32) pairs.
 template <typename S, int MODE, bool RECORD, bool CENTRAL, bool POLY = false>
@@ -37,10 +54,33 @@ __global__ void __launch_bounds__(128, 3) pair_step_kernel(const S* src, S* dst,
                                                         StepCounters* ctr) {
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t xa = blockIdx.x * (2 * blockDim.x) + warp * 64 + lane;
-  const uint32_t xb = xa + 32;
   if (xa >= g.nx) return;
-  node_update2<S, MODE, RECORD, CENTRAL, POLY>(src, dst, g, xa, xb, xb < g.nx, blockIdx.y,
-                                               blockIdx.z, cp, gamma_out, ctr);
+  const bool vb = xa + 32 < g.nx;
+  node_update2<S, MODE, RECORD, CENTRAL, POLY>(src, dst, g, xa, blockIdx.y, blockIdx.z,
+                                               vb ? xa + 32 : xa, blockIdx.y, blockIdx.z, vb,
+                                               cp, gamma_out, ctr);
+}
+
+// The same update over the box's node order instead of rows: block k covers nodes
+// [256 k, 256 k + 256), each warp 64 of them as pairs (n, n + 32), which may straddle rows.
+// For row lengths that are not a multiple of 64 this keeps every lane busy, at the price of
+// two divisions per thread for the coordinates and of two coordinate triples kept live.
+template <typename S, int MODE, bool RECORD, bool CENTRAL, bool POLY = false>
+__global__ void __launch_bounds__(128, 3) pair_linear_kernel(const S* src, S* dst, Geo g,
+                                                          CollideParams cp, float* gamma_out,
+                                                          StepCounters* ctr) {
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t n = blockIdx.x * 256 + warp * 64 + lane;  // P < 2^31
+  if (n >= g.P) return;
+  const uint32_t row = n / g.nx;
+  const uint32_t xa = n - row * g.nx;
+  const uint32_t za = row / g.ny;
+  const uint32_t ya = row - za * g.ny;
+  uint32_t xb = xa, yb = ya, zb = za;
+  const bool vb = n + 32 < g.P;
+  if (vb) advance_node(xb, yb, zb, 32, g.nx, g.ny);
+  node_update2<S, MODE, RECORD, CENTRAL, POLY, false>(src, dst, g, xa, ya, za, xb, yb, zb, vb,
+                                                      cp, gamma_out, ctr);
 }
 
 // Warps per block of the pair kernel: a row needs ceil(nx / 64) warps; blocks of w <= 4 warps
@@ -60,12 +100,19 @@ inline uint32_t pair_block_warps(uint32_t nx) {
 }
 
 // Blocks of whole row segments (a persistent grid measured slower on GB300), sized by
-// pair_block_warps.
+// pair_block_warps; when that leaves more than 5 % of the lanes without a node (rows that are
+// not close to a multiple of 64 nodes long), blocks of 256 consecutive nodes instead.
 template <typename S, int MODE, bool RECORD, bool CENTRAL, bool POLY = false>
 static cudaError_t launch_pair(const S* src, S* dst, const Geo& g, const CollideParams& cp,
                                float* gamma_out, StepCounters* ctr, cudaStream_t st) {
   const uint32_t warps = pair_block_warps(g.nx);
-  const dim3 grid((g.nx + 64 * warps - 1) / (64 * warps), g.ny, g.nz);
+  const uint32_t row_blocks = (g.nx + 64 * warps - 1) / (64 * warps);
+  if (20 * (uint64_t)g.nx < 19 * (uint64_t)row_blocks * 64 * warps) {
+    pair_linear_kernel<S, MODE, RECORD, CENTRAL, POLY>
+        <<<(unsigned)((g.P + 255) / 256), 128, 0, st>>>(src, dst, g, cp, gamma_out, ctr);
+    return cudaGetLastError();
+  }
+  const dim3 grid(row_blocks, g.ny, g.nz);
   pair_step_kernel<S, MODE, RECORD, CENTRAL, POLY><<<grid, 32 * warps, 0, st>>>(
       src, dst, g, cp, gamma_out, ctr);
   return cudaGetLastError();
@@ -138,29 +185,25 @@ __global__ void __launch_bounds__(128, 3) batch_pair_kernel(const BoxDesc* __res
     cp.gamma_mode = gamma_mode;
     const S* src = (const S*)bd.pop[MODE == MODE_PULL ? parity : 0];
     S* dst = (S*)bd.pop[MODE == MODE_PULL ? (parity ^ 1) : 0];
-    // warp q of the item handles 64-node chunk (q mod nchunk) of row (q / nchunk); the warp
-    // index advances by the block's warp count, and chunk, y and z follow it incrementally
-    // (no integer division per unit). blockDim.x is 128 for this kernel.
-    const uint32_t nchunk = (bd.nx + 63) / 64;
-    const uint32_t nq = (uint32_t)w.nrows * nchunk;
+    // The item's rows are one contiguous range of nodes: warp q handles its nodes
+    // [64 q, 64 q + 64) as pairs (n, n + 32), so rows of any length keep every lane busy
+    // (rows shorter or longer than a multiple of 64 nodes share warps). The coordinates of
+    // a advance by the block's 256 nodes per iteration, those of b are a's plus 32; a row
+    // crossing costs one division, none otherwise. blockDim.x is 128 for this kernel.
+    const uint32_t nodes = bd.nx * (uint32_t)w.nrows;
     const uint32_t wstep = blockDim.x >> 5, slot = threadIdx.x & 31;
-    uint32_t q = threadIdx.x >> 5;
-    uint32_t rr = q / nchunk, chunk = q - rr * nchunk;
-    const uint32_t row = (uint32_t)w.row0 + rr;
-    uint32_t z = row / bd.ny, y = row - z * bd.ny;
-    for (; q < nq; q += wstep) {
-      const uint32_t xa = chunk * 64 + slot, xb = xa + 32;
-      if (xa < bd.nx)
-        node_update2<S, MODE, RECORD, CENTRAL>(src, dst, g, xa, xb, xb < bd.nx, y, z, cp,
-                                               bd.gamma, bd.ctr);
-      chunk += wstep;
-      while (chunk >= nchunk) {
-        chunk -= nchunk;
-        if (++y == bd.ny) {
-          y = 0;
-          ++z;
-        }
-      }
+    const uint32_t stride = 64 * wstep;
+    uint32_t la = 64 * (threadIdx.x >> 5) + slot;
+    uint32_t za = (uint32_t)w.row0 / bd.ny;
+    uint32_t ya = (uint32_t)w.row0 - za * bd.ny, xa = 0;
+    advance_node(xa, ya, za, la, bd.nx, bd.ny);
+    for (; la < nodes; la += stride) {
+      uint32_t xb = xa, yb = ya, zb = za;
+      const bool vb = la + 32 < nodes;
+      if (vb) advance_node(xb, yb, zb, 32, bd.nx, bd.ny);
+      node_update2<S, MODE, RECORD, CENTRAL, false, false>(src, dst, g, xa, ya, za, xb, yb, zb,
+                                                           vb, cp, bd.gamma, bd.ctr);
+      advance_node(xa, ya, za, stride, bd.nx, bd.ny);
     }
   }
 }
