@@ -387,6 +387,16 @@ def _torch():
     return torch
 
 
+def _device_buffer(torch, nbytes, device, stream):
+    """The caller-owned device buffer of a context: a torch uint8 tensor. When the library's
+    stream is not the one torch allocated on, the tensor is recorded on it, so that the caching
+    allocator does not hand the memory out again while kernels enqueued there may still run."""
+    buf = torch.empty(nbytes, dtype=torch.uint8, device=device)
+    if stream != torch.cuda.current_stream(device):
+        buf.record_stream(stream)
+    return buf
+
+
 class Lattice:
     """One periodic box. Device memory is a torch uint8 tensor owned by this object."""
 
@@ -401,7 +411,7 @@ class Lattice:
             raise LBError(LB_ERR_INVALID_ARG, "invalid configuration")
         self.device = torch.device(device or "cuda")
         self.stream = stream or torch.cuda.current_stream(self.device)
-        self.buf = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
+        self.buf = _device_buffer(torch, self.nbytes, self.device, self.stream)
         self.ctx = lb_create(self.cfg, self.buf.data_ptr(), self.nbytes, self.stream.cuda_stream)
 
     def close(self):
@@ -568,7 +578,7 @@ class Batch:
             raise LBError(LB_ERR_INVALID_ARG, "invalid batch configuration")
         self.device = torch.device(device or "cuda")
         self.stream = stream or torch.cuda.current_stream(self.device)
-        self.buf = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
+        self.buf = _device_buffer(torch, self.nbytes, self.device, self.stream)
         self.handle = lb_batch_create(self.cfgs, self.buf.data_ptr(), self.nbytes,
                                       self.stream.cuda_stream)
         self.nodes = sum(c.nx * c.ny * c.nz for c in self.cfgs)
