@@ -556,6 +556,23 @@ def test_batch_step_longer_than_one_graph(kbc):
         ref.close()
 
 
+
+def test_side_stream_matches_default_stream(kbc):
+    """A context on a caller-made stream (its buffer recorded on that stream) steps exactly as
+    one on torch's current stream."""
+    import torch
+    f0 = seeded_state(12, 10, 9, seed=4)
+    side = torch.cuda.Stream()
+    out = []
+    for st in (None, side):
+        lat = lb.Lattice(12, 10, 9, storage="f32", scheme="aa", stream=st)
+        lat.set_populations(f0)
+        lat.step(5)
+        out.append(lat.get_populations())
+        lat.close()
+    assert np.array_equal(out[0], out[1])
+
+
 # ------------------------------------------------------------------ full-size sampled parity
 
 def _sampled_step_check(lat, nsample, tol, rng, half=False):
