@@ -23,8 +23,9 @@
  *                the kernels read or write it in place over the host-device link, no
  *                staging copies); either way the call has finished with it on return.
  *   streams      all work is enqueued on the CUDA stream given to lb_create (NULL = legacy
- *                default stream). lb_step never synchronises; lb_moments, lb_diagnostics,
- *                lb_get_populations and lb_set_populations synchronise the stream.
+ *                default stream). lb_step and lb_batch_step never synchronise; lb_moments,
+ *                lb_diagnostics, lb_get_populations, lb_set_populations, lb_presolve and
+ *                lb_init_field from host memory synchronise the stream.
  *   errors       every call returns lb_status; no exception crosses the ABI. Errors of
  *                asynchronous kernels surface at the next synchronising call as
  *                LB_ERR_CUDA. lb_last_error() gives a message. A context is used by one host
@@ -44,7 +45,7 @@ typedef int32_t lb_status;
 enum {
   LB_OK = 0,
   LB_ERR_INVALID_ARG = 1,  /* bad size, parameter, pointer or enum value */
-  LB_ERR_OOM = 2,          /* the buffer passed to lb_create is smaller than required */
+  LB_ERR_OOM = 2,          /* a caller buffer is smaller than required, or host memory ran out */
   LB_ERR_CUDA = 3,         /* a CUDA call or kernel failed (message in lb_last_error) */
   LB_ERR_NONFINITE = 4,    /* lb_diagnostics found NaN/Inf populations */
   LB_ERR_TIMEOUT = 5,      /* a bounded device-side wait ran out */
