@@ -109,7 +109,8 @@ typedef struct {
   int32_t reserved;
   double dudx2;             /* <(d u'_x / d x)^2> */
   double skewness[4];       /* longitudinal skewness factors S_11^n, n = 3..6 (Table 2):
-                               (-1)^n <(d u'_x/d x)^n> <(d u'_x/d x)^2>^(-n/2) */
+                               (-1)^n <(d u'_x/d x)^n> <(d u'_x/d x)^2>^(-n/2);
+                               NaN when dudx2 is 0 (no x-gradient, e.g. at rest) */
 } lb_diag;
 
 /* Gap between the stabilizer estimate eq:result21 and the exact root gamma* of eq:result1,
