@@ -92,3 +92,43 @@ def test_equilibrium_choice_is_validated(lib):
     with pytest.raises(lb.LBError) as e:     # refused on the host, before any device call
         lb.lb_create(lb.make_config(32, gamma="exact", equilibrium="poly2"), 256, 1 << 30, 0)
     assert e.value.status == lb.LB_ERR_UNSUPPORTED
+
+
+def test_binding_structs_and_enums_match_the_header(tmp_path):
+    """The ctypes mirrors of lb_config, lb_diag and lb_gap have the C layout (size and every
+    field offset, as gcc lays out the header), and the binding's enum values are the header's."""
+    import subprocess
+    from paper_1507_02518_gb300 import lb
+    structs = {"lb_config": lb.lb_config, "lb_diag": lb.lb_diag, "lb_gap": lb.lb_gap}
+    enums = ["LB_OK", "LB_ERR_INVALID_ARG", "LB_ERR_OOM", "LB_ERR_CUDA", "LB_ERR_NONFINITE",
+             "LB_ERR_TIMEOUT", "LB_ERR_UNSUPPORTED", "LB_S_D", "LB_S_DT", "LB_S_DQ", "LB_S_DTQ",
+             "LB_S_CD", "LB_S_CDT", "LB_S_CDQ", "LB_S_CDTQ", "LB_GAMMA_ESTIMATE", "LB_GAMMA_LBGK",
+             "LB_GAMMA_RLB", "LB_GAMMA_EXACT", "LB_F64", "LB_F32", "LB_F16", "LB_PULL", "LB_AA",
+             "LB_EQ_PRODUCT", "LB_EQ_POLY2", "LB_KERNEL_AUTO", "LB_KERNEL_DIRECT",
+             "LB_KERNEL_STAGED", "LB_KERNEL_PERSISTENT", "LB_KERNEL_PACKED"]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "kbc_lb.h"',
+             "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append('printf("%s sizeof %%zu\\n", sizeof(%s));' % (name, name))
+        for field, _ in cls._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));'
+                         % (name, field, name, field))
+    for e in enums:
+        lines.append('printf("enum %s %%d\\n", (int)%s);' % (e, e))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    got = {}
+    for line in out.splitlines():
+        *key, value = line.split()
+        got[tuple(key)] = int(value)
+    for name, cls in structs.items():
+        assert got[(name, "sizeof")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
+    for e in enums:
+        assert got[("enum", e)] == getattr(lb, e), e
