@@ -67,9 +67,8 @@ VARIANTS = [
      "gamma": "exact", "gap": True},
 ]
 # FP64-pipe instructions per lattice update of step_kernel<double> (ncu: the FP64 pipe was
-# 86.8 % busy over 2.19 ms for 2,097,152 nodes, 571 instructions per node;
-# profiles/step_kernel_f64_pull_hit128.md) and the GB300 FP64 pipe peak of 2 instructions per
-# SM per cycle.
+# 86.8 % busy over 2.19 ms for 2,097,152 nodes, 571 instructions per node, on a 128^3 FP64
+# pull box) and the GB300 FP64 pipe peak of 2 instructions per SM per cycle.
 FP64_INSTR_PER_LUP = 571.0
 FP64_PIPE_PER_SM_PER_CYCLE = 2.0
 # DRAM bytes per lattice update of the default FP32 pull step kernel (packed FP32x2) from an ncu
@@ -77,7 +76,7 @@ FP64_PIPE_PER_SM_PER_CYCLE = 2.0
 # it is profiled again.
 NCU_TRAFFIC_PER_LUP = {
     # pair_step_kernel<float, MODE_PULL>, the bench's own launch on 256^3: 1811.99 MB read +
-    # 1757.02 MB written for 16,777,216 nodes (profiles/pair_step_kernel_f32_pull_hit256.md)
+    # 1757.02 MB written for 16,777,216 nodes
     "1301ce4996f266c0": 3569.00e6 / 16777216,
 }
 
@@ -106,12 +105,21 @@ def parse_workload(name):
     return w
 
 
+KERNEL_SOURCES = ("kbc_device.cuh", "kbc_kernels.cuh", "kbc_staged.cuh", "kbc_tma.cuh",
+                  "kbc_ops.h", "kbc_f32.cu", "kbc_f16.cu", "lb_api.cu")
+
+
 def kernel_source_hash() -> str:
+    """Hash of every source that decides the step kernels' code and launch shapes (kernel
+    bodies, kernel selection and launch configuration)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1507_02518_gb300", "csrc")
-    for name in ("kbc_device.cuh", "kbc_kernels.cuh", "kbc_f32.cu"):
-        with open(os.path.join(csrc, name), "rb") as fh:
-            h.update(fh.read())
+    for name in KERNEL_SOURCES:
+        path = os.path.join(csrc, name)
+        if os.path.exists(path):
+            with open(path, "rb") as fh:
+                h.update(name.encode())
+                h.update(fh.read())
     return h.hexdigest()[:16]
 
 

@@ -3,10 +3,10 @@
  *
  * Method: Boesch, Chikatamarla, Karlin, "Entropic multi-relaxation lattice Boltzmann scheme
  * for turbulent flows" (arXiv:1507.02518). One time step is eq:Egeneral on a periodic box:
- * every node collides with the KBC operator (collision listing of Sec. KBC: rho, u ->
- * product-form equilibrium eq:entropic_eq -> shear part s from Table 1 -> ds, dh ->
- * stabilizer gamma by eq:result21 -> f' = f - beta(2 ds + gamma dh)) and the post-collision
- * populations propagate along the 27 links.
+ * every node collides with the KBC operator (Sec. KBC: the mirror state eq:ksh-mirror in
+ * eq:Egeneral, i.e. f' = f - beta(2 ds + gamma dh) with ds = s - s_eq from Table 1 and the
+ * product-form equilibrium eq:entropic_eq, dh = f - f_eq - ds, and the stabilizer gamma of
+ * eq:result21) and the post-collision populations propagate along the 27 links.
  *
  * Conventions
  *   velocities   i = (vx+1) + 3*(vy+1) + 9*(vz+1), v in {-1,0,1}^3 (eq:D3Q27vel); the opposite

@@ -195,7 +195,7 @@ def collide_mirror(f, beta_, variant, gamma):
 
 
 def deltas(f, variant=S_DTQ):
-    """(f_eq, ds, dh) of the collision listing, steps 2-5."""
+    """(f_eq, ds, dh) of Sec. KBC: the equilibrium, ds = s - s_eq and dh = f - f_eq - ds."""
     f = _f64(f)
     feq, ds, dh = np.zeros(27), np.zeros(27), np.zeros(27)
     lib().orc_deltas(_p(f), int(variant), _p(feq), _p(ds), _p(dh))
@@ -308,6 +308,8 @@ def presolve(u0, beta_pre, max_iters, tol=-1.0, f=None):
     res = ctypes.c_double()
     it = lib().orc_presolve(nx, ny, nz, _p(f), _p(fb), _p(u0), float(beta_pre), int(max_iters),
                             float(tol), ctypes.byref(res))
+    if it < 0:
+        raise MemoryError("orc_presolve could not allocate its work array")
     return f, int(it), res.value
 
 

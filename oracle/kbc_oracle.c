@@ -16,9 +16,13 @@
  *   central moments and central parts ... Sec. "Moment System" and the appendix (eq:cm1-eq:cm23,
  *                                           eq:cmf000-eq:cmfxyz), as tensor products of the
  *                                           one-dimensional central inverse
- *   collision ........................... the 7-step collision listing of Sec. KBC:
- *                                           rho,u -> f_eq -> s, s_eq -> ds -> dh -> gamma
- *                                           (eq:result21) -> f' = f - beta(2 ds + gamma dh)
+ *   collision ........................... eq:Egeneral with the mirror state eq:ksh-mirror
+ *                                           (Sec. KBC): with ds = s - s_eq and
+ *                                           dh = h - h_eq = f - f_eq - ds (k = k_eq, since k
+ *                                           depends on the conserved fields only),
+ *                                           f' = (1 - beta) f + beta f_mirr
+ *                                              = f - beta (2 ds + gamma dh),
+ *                                           gamma from eq:result21
  *   mirror form ......................... eq:Egeneral with eq:ksh-mirror (second route)
  *   exact stabilizer .................... root of eq:result1 (Newton iteration)
  *   streaming ........................... left-hand side of eq:Egeneral, periodic box
@@ -30,6 +34,7 @@
 #include "kbc_oracle.h"
 
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
 #include <omp.h>
@@ -304,19 +309,21 @@ static void groups(const double *f, int variant, double *rho, double *u, double 
   }
 }
 
-/* collision listing, steps 1-5: f_eq, ds = s - s_eq, dh = f - f_eq - ds */
+/* The deviations of Sec. KBC: f_eq(rho, u) (eq:entropic_eq, or eq:polynomial2), the shear
+ * deviation ds = s - s_eq (s from Table 1 on the moments of f, s_eq from Table 1 on the moments
+ * of f_eq), and dh = h - h_eq = f - f_eq - ds (eq:ksh-representation with k = k_eq). */
 void orc_deltas(const double *f, int variant, double *feq, double *ds, double *dh) {
   double rho, u[3], rho_eq, u_eq[3];
   double k[27], d[27], t[27], q[27], s[27];
   double keq[27], deq[27], teq[27], qeq[27], seq[27];
-  groups(f, variant, &rho, u, k, d, t, q);           /* step 1: rho, u; step 3: s */
-  equilibrium_of(variant, rho, u, feq);              /* step 2 */
+  groups(f, variant, &rho, u, k, d, t, q);           /* rho, u and the groups of f */
+  equilibrium_of(variant, rho, u, feq);
   groups(feq, variant, &rho_eq, u_eq, keq, deq, teq, qeq);  /* s_eq from the moments of f_eq */
   shear_part(d, t, q, variant, s);
   shear_part(deq, teq, qeq, variant, seq);
   for (int i = 0; i < 27; ++i) {
-    ds[i] = s[i] - seq[i];                           /* step 4 */
-    dh[i] = f[i] - feq[i] - ds[i];                   /* step 5 */
+    ds[i] = s[i] - seq[i];
+    dh[i] = f[i] - feq[i] - ds[i];
   }
 }
 
@@ -343,11 +350,12 @@ int orc_collide(const double *f, double beta, int variant, int gamma_mode, doubl
       gamma = 2.0;
       guarded = 1;
     } else {
-      gamma = 1.0 / beta - (2.0 - 1.0 / beta) * num / den;   /* step 6, eq:result21 */
+      gamma = 1.0 / beta - (2.0 - 1.0 / beta) * num / den;   /* eq:result21 */
       if (gamma_mode == ORC_GAMMA_EXACT) gamma = orc_gamma_exact(feq, ds, dh, beta, gamma);
     }
   }
-  for (int i = 0; i < 27; ++i) fout[i] = f[i] - beta * (2.0 * ds[i] + gamma * dh[i]); /* step 7 */
+  /* eq:Egeneral with eq:ksh-mirror: (1 - beta) f + beta f_mirr = f - beta (2 ds + gamma dh) */
+  for (int i = 0; i < 27; ++i) fout[i] = f[i] - beta * (2.0 * ds[i] + gamma * dh[i]);
   if (gamma_out) *gamma_out = gamma;
   return guarded;
 }
@@ -569,14 +577,19 @@ int64_t orc_run(int32_t nx, int32_t ny, int32_t nz, double *fa, double *fb, int6
  *   f <- S[ f - 2 beta_pre (f - f_eq(rho(f), u0)) ],   S = propagation (orc_stream),
  * whose density relaxes to the steady state of its mass balance. After each iteration the
  * change max_x |rho^{n+1}(x) - rho^n(x)| is measured; the loop stops after the first
- * iteration whose change is <= tol, or after max_iters. Returns the iterations run;
- * *residual = the last change (NaN when none was run). fb is scratch of the size of f. */
+ * iteration whose change is <= tol, or after max_iters. Returns the iterations run, or -1
+ * when its work array cannot be allocated; *residual = the last change (NaN when none was
+ * run). fb is scratch of the size of f. */
 int64_t orc_presolve(int32_t nx, int32_t ny, int32_t nz, double *f, double *fb, const double *u0,
                      double beta_pre, int64_t max_iters, double tol, double *residual) {
   const int64_t P = (int64_t)nx * ny * nz;
   double *rho_old = (double *)malloc((size_t)P * sizeof(double));
   double res = NAN;
   int64_t it = 0;
+  if (!rho_old) {
+    if (residual) *residual = NAN;
+    return -1;
+  }
   for (int64_t n = 0; n < P; ++n) {
     double r = 0.0;
     for (int i = 0; i < 27; ++i) r += f[i * P + n];

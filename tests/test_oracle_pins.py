@@ -224,7 +224,8 @@ def test_rlb_special_case_relaxes_higher_moments_to_equilibrium():
 
 @pytest.mark.parametrize("variant", range(4))
 def test_mirror_form_equals_relaxation_form(variant):
-    """eq:Egeneral + eq:ksh-mirror == the listing's f' = f - beta(2 ds + gamma dh)."""
+    """eq:Egeneral + eq:ksh-mirror built from explicit k, s, h parts == the relaxation form
+    f' = f - beta(2 ds + gamma dh) that the two reduce to."""
     rng = np.random.default_rng(11 + variant)
     f = near_eq_population(rng)
     fo, g, _ = oracle.collide(f, BETA, variant)
