@@ -90,8 +90,11 @@ typedef struct {
 } lb_config;
 
 /* Diagnostics of Sec. "Numerical Simulations" at the current time t. Averages <.> are over
- * nodes; u' = u - <u>; gradients are central differences of order grad_order: 2 (the
- * default, as for the paper's enstrophy curves) or 8 (Table 2), see lb_set_diag_order. */
+ * nodes; u' = u - <u> (k is summed in a second pass over the field, after <u>); gradients
+ * are central differences of order grad_order: 2 (the default, as for the paper's enstrophy
+ * curves) or 8 (Table 2), see lb_set_diag_order. In a field holding NaN/Inf the averages
+ * run over the nodes whose rho and u (k, <u>, gamma) or velocity gradients (Omega, epsilon,
+ * dudx2, skewness) are finite, and the call returns LB_ERR_NONFINITE. */
 typedef struct {
   int64_t step;             /* t */
   int64_t nodes;            /* P */
@@ -257,32 +260,39 @@ lb_status lb_set_prefetch(lb_ctx *ctx, int32_t items_ahead);
  * bx*by in {64, 128, 256, 512} (at most 256 for LB_F64) and bx a multiple of 32. */
 lb_status lb_set_block(lb_ctx *ctx, int32_t bx, int32_t by);
 
-/* Bound on every device-side wait of the staged kernel, in SM clock cycles (default 2e9,
- * about one second). When a wait runs out the kernel sets a flag and returns; the next
- * synchronising call returns LB_ERR_TIMEOUT and the state is not valid. stall_copies != 0
+/* Bound on every device-side wait of the staged kernels, in SM clock cycles (default 2e9,
+ * about one second). When a wait runs out the kernel sets a flag, waits (with the same bound)
+ * for the copies it has issued, and returns; the next synchronising call returns
+ * LB_ERR_TIMEOUT and the state is not valid: lb_step, lb_moments, lb_diagnostics,
+ * lb_get_populations, lb_spectrum and lb_stabilizer_gap then return LB_ERR_TIMEOUT until
+ * lb_set_populations, lb_init_field or lb_presolve rewrites the state. stall_copies != 0
  * is a test hook of that path: the staged kernel then issues no copies, so its first wait
  * runs out (use a small budget). */
 lb_status lb_set_wait_budget(lb_ctx *ctx, uint64_t cycles, int32_t stall_copies);
 
 /* Diagnostics of a canonical population field with no memory allocation of any kind.
  * The paper has no counterpart: this entry point exists for callers that cannot allocate
- * device memory when they need diagnostics -- code running while a stream is captured into
- * a CUDA graph, plugins whose host framework owns all device memory, monitors that must not
- * change a job's footprint. It computes the fields of lb_diag that depend on the populations
- * alone (mass, momentum, kinetic_energy, enstrophy, dissipation, nonfinite_count, nodes);
- * gamma_mean and gamma_std are NaN, den_guard_count is 0 and step is -1.
+ * device memory when they need diagnostics -- extensions inside a host framework whose pool
+ * allocator has reserved the device's memory (a cudaMalloc behind its back can fail or
+ * break its accounting), monitors of jobs sized to fill the GPU's memory that must not
+ * change the footprint, and latency-sensitive loops where cudaMalloc/cudaFree would
+ * synchronise the device. It computes the fields of lb_diag that depend on the populations
+ * alone (mass, momentum, kinetic_energy, enstrophy, dissipation, nonfinite_count, nodes),
+ * with the averages of lb_diagnostics at grad_order 2; gamma_mean and gamma_std are NaN,
+ * den_guard_count is 0, dudx2 and skewness are NaN and step is -1.
  *   f       device pointer to FP64 canonical populations f[27][P] (the layout of
  *           lb_get_populations), P = nx*ny*nz <= 65536 nodes; larger boxes return
  *           LB_ERR_INVALID_ARG before any GPU work.
  *   nu      the kinematic viscosity in the dissipation, > 0.
- *   stream  cudaStream_t the work is enqueued on; the call synchronises it.
+ *   stream  cudaStream_t the work is enqueued on; the call synchronises it before returning.
  *   out     host struct, filled on LB_OK and LB_ERR_NONFINITE.
  * The work space is one file-scope __device__ array (about 1.6 MB) that stays on every GPU that
- * loaded the library until the process exits. The first call on a device looks up that
- * array's address with the device current, so make it before any stream capture begins. All
- * calls share the array: calls that overlap on the GPU race and must be serialised by the
- * caller. Errors: LB_ERR_INVALID_ARG, LB_ERR_CUDA, LB_ERR_NONFINITE; lb_last_error(NULL)
- * explains. */
+ * loaded the library until the process exits. The first call on a device does a one-time
+ * set-up, looking up that array's address with the device current; make that first call
+ * before any stream capture begins. All calls share the array and it keeps the last call's
+ * contents (each call clears what it accumulates): calls that overlap on the GPU race and
+ * must be serialised by the caller. Errors: LB_ERR_INVALID_ARG, LB_ERR_CUDA,
+ * LB_ERR_NONFINITE; lb_last_error(NULL) explains. */
 lb_status lb_diagnostics_noalloc(int32_t nx, int32_t ny, int32_t nz, double nu, const double *f,
                                  void *stream, lb_diag *out);
 

@@ -117,10 +117,12 @@ __global__ void moments_kernel(const S* b0, const S* b1, Geo g, int scheme, int 
 }
 
 // ------------------------------------------------------------------ diagnostics
-// Sums (FP64) in partials[block * kDiagSums + j]:
+// Sums (FP64) in partials[block * kDiagSums + j], over the nodes whose rho and u are finite
+// (0-10) or whose velocity gradients are finite (11-19):
 //  0 sum (rho - 1), 1-3 sum rho u, 4-6 sum u, 7 sum |u|^2, 8 sum gamma, 9 sum gamma^2,
 //  10 non-finite nodes, 11 sum |curl u|^2, 12 sum (d_b u_a + d_a u_b)^2,
-//  13-17 sum (d u_x / d x)^n for n = 2..6
+//  13-17 sum (d u_x / d x)^n for n = 2..6, 18 sum |u - <u>|^2 (second pass, with <u> from the
+//  first), 19 nodes with finite gradients
 template <int N>
 __device__ __forceinline__ void block_reduce_store(double (&v)[N], double* dst) {
   __shared__ double sh[32][N];
@@ -236,9 +238,13 @@ template <> struct FdCoef<4> {
 // 256^3; FP64 arithmetic per node would saturate GB300's FP64 pipe), then FP64 from the
 // block reduction on.
 template <typename R, int K>
-__global__ void __launch_bounds__(256) diag_grad_kernel(Geo g, const R* uf, double* partials) {
-  R acc[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+__global__ void __launch_bounds__(256) diag_grad_kernel(Geo g, const R* uf, const double* sums,
+                                                        double* partials) {
+  R acc[9] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
   const uint32_t dims[3] = {g.nx, g.ny, g.nz};
+  // <u> over the finite nodes, from the sums of the first pass
+  const double nfin = (double)g.P - sums[10];
+  const R mean[3] = {(R)(sums[4] / nfin), (R)(sums[5] / nfin), (R)(sums[6] / nfin)};
   for (uint64_t n = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; n < g.P;
        n += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t c[3];
@@ -288,12 +294,16 @@ __global__ void __launch_bounds__(256) diag_grad_kernel(Geo g, const R* uf, doub
         acc[m] += qn;
         qn *= q;
       }
+      acc[8] += R(1);
     }
+    const R d0 = uf[n] - mean[0], d1 = uf[g.P + n] - mean[1], d2 = uf[2 * g.P + n] - mean[2];
+    const R dd = d0 * d0 + d1 * d1 + d2 * d2;
+    if (isfinite(dd)) acc[7] += dd;
   }
-  double v[7];
+  double v[9];
 #pragma unroll
-  for (int j = 0; j < 7; ++j) v[j] = (double)acc[j];
-  block_reduce_store<7>(v, partials + blockIdx.x * kDiagSums + 11);
+  for (int j = 0; j < 9; ++j) v[j] = (double)acc[j];
+  block_reduce_store<9>(v, partials + blockIdx.x * kDiagSums + 11);
 }
 
 // fixed-order final reduction: sums[j] = sum over blocks of partials[block][j]
@@ -562,10 +572,11 @@ cudaError_t Ops<S>::diag(const BoxView& b, int64_t t, bool with_gamma, int order
   else
     diag_fields_kernel<S, 2><<<nblocks, 256, 0, st>>>((const S*)b.pop[0], g, b.gamma, wg,
                                                       (R*)ufield, partials);
+  diag_final_kernel<<<1, 32, 0, st>>>(partials, nblocks, sums);  // <u> for the second pass
   if (order == 8)
-    diag_grad_kernel<R, 4><<<nblocks, 256, 0, st>>>(g, (const R*)ufield, partials);
+    diag_grad_kernel<R, 4><<<nblocks, 256, 0, st>>>(g, (const R*)ufield, sums, partials);
   else
-    diag_grad_kernel<R, 1><<<nblocks, 256, 0, st>>>(g, (const R*)ufield, partials);
+    diag_grad_kernel<R, 1><<<nblocks, 256, 0, st>>>(g, (const R*)ufield, sums, partials);
   diag_final_kernel<<<1, 32, 0, st>>>(partials, nblocks, sums);
   return cudaGetLastError();
 }

@@ -199,6 +199,9 @@ struct lb_ctx {
   int diag_order = 2;
   bool gamma_valid = false;
   bool batch_view = false;
+  // set when a step kernel's bounded wait ran out: the populations are not a valid state
+  // until lb_set_populations, lb_init_field or lb_presolve rewrites them
+  bool needs_reset = false;
   std::string err;
 };
 
@@ -281,10 +284,20 @@ lb_status sync(lb_ctx* c, const char* what) {
   if (flag) {
     cudaMemsetAsync(&c->counters->timeout, 0, sizeof flag, c->stream);
     cudaStreamSynchronize(c->stream);
+    c->needs_reset = true;
     return fail(c, LB_ERR_TIMEOUT, std::string(what) + ": a step kernel's bounded wait for its "
-                                   "staged loads ran out; the state is not valid");
+                                   "staged loads ran out; the state is not valid until "
+                                   "lb_set_populations, lb_init_field or lb_presolve");
   }
   return LB_OK;
+}
+
+// Calls that read or advance the state refuse to run on a state left invalid by a timeout.
+lb_status check_state(lb_ctx* c, const char* what) {
+  if (!c->needs_reset) return LB_OK;
+  return fail(c, LB_ERR_TIMEOUT, std::string(what) + ": the state is not valid after a timed-"
+                                 "out step; call lb_set_populations, lb_init_field or "
+                                 "lb_presolve first");
 }
 
 kbc::StepOpts step_opts(const lb_ctx* c) {
@@ -375,6 +388,7 @@ lb_status lb_init_field(lb_ctx* c, const double* rho, const double* u, int on_de
   Range range_("lb_init_field");
   if (!c) return LB_ERR_INVALID_ARG;
   if (!u) return fail(c, LB_ERR_INVALID_ARG, "u is NULL");
+  c->needs_reset = false;  // the state is rewritten
   const uint64_t P = c->box.P;
   c->t = 0;
   c->gamma_valid = false;
@@ -420,6 +434,10 @@ lb_status lb_presolve(lb_ctx* c, const double* u0, int on_device, double nu_pre,
   if (std::isnan(tol)) return fail(c, LB_ERR_INVALID_ARG, "tol is NaN");
   if (from_current && c->t != 0)
     return fail(c, LB_ERR_INVALID_ARG, "from_current needs the state at t = 0");
+  if (from_current) {
+    if (lb_status cs = check_state(c, "presolve"); cs != LB_OK) return cs;
+  }
+  c->needs_reset = false;  // the state is rewritten
   const uint64_t P = c->box.P;
   const double beta_pre = 1.0 / (6.0 * nu_pre + 1.0);
   c->t = 0;
@@ -511,6 +529,7 @@ lb_status lb_step(lb_ctx* c, int64_t n) {
   Range range_("lb_step");
   if (!c) return LB_ERR_INVALID_ARG;
   if (n < 0) return fail(c, LB_ERR_INVALID_ARG, "n must be >= 0");
+  if (lb_status cs = check_state(c, "step"); cs != LB_OK) return cs;
   for (int64_t k = 0; k < n; ++k) {
     const bool record = (k == n - 1);
     cudaError_t e = cudaSuccess;
@@ -530,6 +549,7 @@ lb_status lb_moments(lb_ctx* c, double* rho, double* u, int on_device) {
   Range range_("lb_moments");
   if (!c) return LB_ERR_INVALID_ARG;
   if (!u) return fail(c, LB_ERR_INVALID_ARG, "u is NULL");
+  if (lb_status cs = check_state(c, "moments"); cs != LB_OK) return cs;
   const uint64_t P = c->box.P;
   cudaError_t e;
   if (!on_device) {  // page-locked outputs: the kernel writes them in place
@@ -565,6 +585,7 @@ lb_status lb_moments(lb_ctx* c, double* rho, double* u, int on_device) {
 lb_status lb_diagnostics(lb_ctx* c, lb_diag* out) {
   Range range_("lb_diagnostics");
   if (!c || !out) return c ? fail(c, LB_ERR_INVALID_ARG, "out is NULL") : LB_ERR_INVALID_ARG;
+  if (lb_status cs = check_state(c, "diagnostics"); cs != LB_OK) return cs;
   cudaError_t e = dispatch(c, [&](auto ops) {
     return ops.diag(c->box, c->t, c->gamma_valid, c->diag_order, c->ufield, c->partials,
                     kbc::kDiagBlocks,
@@ -579,18 +600,20 @@ lb_status lb_diagnostics(lb_ctx* c, lb_diag* out) {
   if (e != cudaSuccess) return cuda_fail(c, e, "copying diagnostics");
   lb_status st = sync(c, "diagnostics");
   if (st != LB_OK) return st;
+  // averages over the nodes whose moments (Pf) or velocity gradients (Pg) are finite; with a
+  // field free of NaN/Inf both are P
   const double P = (double)c->box.P;
+  const double Pf = P - s[10], Pg = s[19];
   out->step = c->t;
   out->nodes = (int64_t)c->box.P;
-  out->mass = (P - s[10]) + s[0];  // finite nodes: their count plus the sum of rho - 1
+  out->mass = Pf + s[0];  // finite nodes: their count plus the sum of rho - 1
   for (int a = 0; a < 3; ++a) out->momentum[a] = s[1 + a];
-  const double mx = s[4] / P, my = s[5] / P, mz = s[6] / P;
-  out->kinetic_energy = 0.5 * (s[7] / P - (mx * mx + my * my + mz * mz));
-  out->enstrophy = 0.5 * s[11] / P;
-  out->dissipation = 0.5 * c->cfg.nu * s[12] / P;
+  out->kinetic_energy = 0.5 * s[18] / Pf;  // k = 1/2 <|u - <u>|^2>, two passes
+  out->enstrophy = 0.5 * s[11] / Pg;
+  out->dissipation = 0.5 * c->cfg.nu * s[12] / Pg;
   if (c->gamma_valid) {
-    const double gm = s[8] / P;
-    const double var = s[9] / P - gm * gm;
+    const double gm = s[8] / Pf;
+    const double var = s[9] / Pf - gm * gm;
     out->gamma_mean = gm;
     out->gamma_std = var > 0.0 ? std::sqrt(var) : 0.0;
     out->den_guard_count = (int64_t)ctr.guarded;
@@ -601,10 +624,10 @@ lb_status lb_diagnostics(lb_ctx* c, lb_diag* out) {
   }
   out->grad_order = c->diag_order;
   out->reserved = 0;
-  const double m2 = s[13] / P;
+  const double m2 = s[13] / Pg;
   out->dudx2 = m2;
   for (int m = 3; m <= 6; ++m)
-    out->skewness[m - 3] = (m % 2 ? -1.0 : 1.0) * (s[13 + m - 2] / P) / std::pow(m2, 0.5 * m);
+    out->skewness[m - 3] = (m % 2 ? -1.0 : 1.0) * (s[13 + m - 2] / Pg) / std::pow(m2, 0.5 * m);
   out->nonfinite_count = (int64_t)s[10];
   if (out->nonfinite_count > 0) {
     char buf[96];
@@ -637,6 +660,7 @@ lb_status lb_spectrum(lb_ctx* c, void* work, size_t work_bytes, int32_t nbins, d
   Range range_("lb_spectrum");
   if (!c) return LB_ERR_INVALID_ARG;
   if (!work || !E) return fail(c, LB_ERR_INVALID_ARG, "work or E is NULL");
+  if (lb_status cs = check_state(c, "spectrum"); cs != LB_OK) return cs;
   lb_status st;
   if (!spectrum_args(c, nbins, &st)) return st;
   if (((uintptr_t)work % kAlign) != 0)
@@ -665,6 +689,7 @@ lb_status lb_set_diag_order(lb_ctx* c, int32_t order) {
 lb_status lb_stabilizer_gap(lb_ctx* c, lb_gap* out) {
   Range range_("lb_stabilizer_gap");
   if (!c || !out) return c ? fail(c, LB_ERR_INVALID_ARG, "out is NULL") : LB_ERR_INVALID_ARG;
+  if (lb_status cs = check_state(c, "stabilizer gap"); cs != LB_OK) return cs;
   if (c->box.poly)
     return fail(c, LB_ERR_UNSUPPORTED, "the stabilizer gap is built for the product-form "
                                        "equilibrium only");
@@ -693,6 +718,7 @@ lb_status lb_get_populations(lb_ctx* c, double* f, int on_device) {
   Range range_("lb_get_populations");
   if (!c) return LB_ERR_INVALID_ARG;
   if (!f) return fail(c, LB_ERR_INVALID_ARG, "f is NULL");
+  if (lb_status cs = check_state(c, "get_populations"); cs != LB_OK) return cs;
   const uint64_t P = c->box.P;
   cudaError_t e;
   if (!on_device && mapped_host(f)) {  // page-locked output: written in place
@@ -720,6 +746,7 @@ lb_status lb_set_populations(lb_ctx* c, const double* f, int on_device) {
   Range range_("lb_set_populations");
   if (!c) return LB_ERR_INVALID_ARG;
   if (!f) return fail(c, LB_ERR_INVALID_ARG, "f is NULL");
+  c->needs_reset = false;  // the state is rewritten
   const uint64_t P = c->box.P;
   c->gamma_valid = false;
   cudaError_t e;

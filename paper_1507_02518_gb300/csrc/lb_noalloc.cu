@@ -1,22 +1,33 @@
 // lb_noalloc.cu -- diagnostics of a population field without any memory allocation.
 //
-// Some callers cannot allocate device memory at the moment they want diagnostics: code that
-// runs while a CUDA stream is being captured into a graph (cudaMalloc is not allowed there),
-// plugins whose host framework owns every device allocation through its own pool, and
-// monitoring hooks that must not change a job's memory footprint between steps. For them this
-// file offers lb_diagnostics_noalloc: the caller passes the populations (device memory it
-// already holds) and a host struct for the result, and the work space comes from one
-// file-scope __device__ array that the library image carries on every GPU that loads it.
+// Some callers cannot allocate device memory at the moment they want diagnostics:
+//   * extensions running inside a host framework that reserves the device's memory through
+//     its own pool allocator: a cudaMalloc behind the pool's back can fail once the pool has
+//     taken the GPU's free memory, and memory the pool does not know about breaks its
+//     accounting;
+//   * monitoring hooks of long jobs whose populations were sized to fill the GPU's memory:
+//     there is no room left for a diagnostics work buffer, and the hook must not change the
+//     job's footprint between steps;
+//   * latency-sensitive loops: cudaMalloc and cudaFree can synchronise the whole device and
+//     stall the work of other streams.
+// For them this file offers lb_diagnostics_noalloc: the caller passes the populations (device
+// memory it already holds) and a host struct for the result, and the work space comes from
+// one file-scope __device__ array that the library image carries on every GPU that loads it.
 //
 // Limits and behaviour, stated for users:
 //   * at most kNoallocMaxNodes = 65,536 lattice nodes per call (e.g. 40^3 or 64x32x32); larger
 //     boxes are rejected with LB_ERR_INVALID_ARG before any GPU work;
 //   * the array (about 1.6 MB) stays resident on each GPU that loaded the library until the
 //     process exits;
-//   * the first call on a device looks up the array's device address with the device current;
-//     make that first call before any stream capture begins;
-//   * every call shares the one array per device, so calls that overlap on the GPU (different
-//     streams, or different host threads) race on it; issue them one after another.
+//   * the first call on a device does a one-time set-up: it looks up the array's device
+//     address (cudaGetSymbolAddress) with that device current; make that first call before
+//     any stream capture begins;
+//   * every call shares the one array per device and keeps the last call's contents (the
+//     call clears the sums it accumulates before using them), so calls that overlap on the
+//     GPU (different streams, or different host threads) race on it; issue them one after
+//     another;
+//   * the call enqueues its kernels on the given stream and synchronises that stream before
+//     it returns.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -81,8 +92,9 @@ __device__ __forceinline__ void na_block_sum(double (&v)[N], double* dst) {
   }
 }
 
-// rho, rho u and u of every node of the canonical field f[27][P]; partial sums per block:
-// 0 sum rho, 1-3 sum rho u, 4-6 sum u, 7 sum |u|^2, 10 non-finite nodes
+// rho, rho u and u of every node of the canonical field f[27][P]; partial sums per block over
+// the nodes whose rho and u are finite: 0 sum rho, 1-3 sum rho u, 4-6 sum u, 7 sum |u|^2,
+// and 10 the number of non-finite nodes
 __global__ void __launch_bounds__(kNaThreads) na_fields_kernel(const double* __restrict__ f,
                                                                NaGeo g, double* scratch) {
   double* uf = scratch;
@@ -117,11 +129,16 @@ __global__ void __launch_bounds__(kNaThreads) na_fields_kernel(const double* __r
   na_block_sum<11>(v, partials + blockIdx.x * kNaSums);
 }
 
-// second-order central differences of u: 11 sum |curl u|^2, 12 sum (d_b u_a + d_a u_b)^2
+// Second pass, after the first pass's sums are reduced: second-order central differences of
+// u over the nodes whose gradients are finite, 11 sum |curl u|^2, 12 sum (d_b u_a + d_a u_b)^2,
+// 13 their number; and 14 sum |u - <u>|^2 over the finite nodes, <u> from the first pass.
 __global__ void __launch_bounds__(kNaThreads) na_grad_kernel(NaGeo g, double* scratch) {
   const double* uf = scratch;
   double* partials = scratch + 3 * (size_t)kNoallocMaxNodes;
-  double v[2] = {0.0, 0.0};
+  const double* sums = partials + (size_t)kNaBlocks * kNaSums;
+  const double nfin = (double)g.P - sums[10];
+  const double mean[3] = {sums[4] / nfin, sums[5] / nfin, sums[6] / nfin};
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
   for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < g.P; n += gridDim.x * blockDim.x) {
     uint32_t x, y, z;
     na_coords(g, n, x, y, z);
@@ -146,9 +163,14 @@ __global__ void __launch_bounds__(kNaThreads) na_grad_kernel(NaGeo g, double* sc
     if (isfinite(ww) && isfinite(ss)) {
       v[0] += ww;
       v[1] += ss;
+      v[2] += 1.0;
     }
+    const double d0 = uf[n] - mean[0], d1 = uf[g.P + n] - mean[1];
+    const double d2 = uf[2 * (size_t)g.P + n] - mean[2];
+    const double dd = d0 * d0 + d1 * d1 + d2 * d2;
+    if (isfinite(dd)) v[3] += dd;
   }
-  na_block_sum<2>(v, partials + blockIdx.x * kNaSums + 11);
+  na_block_sum<4>(v, partials + blockIdx.x * kNaSums + 11);
 }
 
 __global__ void na_final_kernel(double* scratch) {
@@ -231,6 +253,7 @@ lb_status lb_diagnostics_noalloc(int32_t nx, int32_t ny, int32_t nz, double nu, 
   cudaError_t e = cudaMemsetAsync(partials, 0, sizeof(double) * (kNaBlocks * kNaSums + kNaSums), st);
   if (e == cudaSuccess) {
     na_fields_kernel<<<kNaBlocks, kNaThreads, 0, st>>>(f, g, scratch);
+    na_final_kernel<<<1, 32, 0, st>>>(scratch);  // <u> for the second pass
     na_grad_kernel<<<kNaBlocks, kNaThreads, 0, st>>>(g, scratch);
     na_final_kernel<<<1, 32, 0, st>>>(scratch);
     e = cudaGetLastError();
@@ -242,16 +265,16 @@ lb_status lb_diagnostics_noalloc(int32_t nx, int32_t ny, int32_t nz, double nu, 
     kbc_set_thread_error(std::string("diagnostics without allocation: ") + cudaGetErrorString(e));
     return LB_ERR_CUDA;
   }
-  const double Pd = (double)P;
+  // averages over the nodes whose moments (Pf) or velocity gradients (Pg) are finite
+  const double Pf = (double)P - h[10], Pg = h[13];
   memset(out, 0, sizeof *out);
   out->step = -1;
   out->nodes = (int64_t)P;
   out->mass = h[0];
   for (int a = 0; a < 3; ++a) out->momentum[a] = h[1 + a];
-  const double mx = h[4] / Pd, my = h[5] / Pd, mz = h[6] / Pd;
-  out->kinetic_energy = 0.5 * (h[7] / Pd - (mx * mx + my * my + mz * mz));
-  out->enstrophy = 0.5 * h[11] / Pd;
-  out->dissipation = 0.5 * nu * h[12] / Pd;
+  out->kinetic_energy = 0.5 * h[14] / Pf;  // k = 1/2 <|u - <u>|^2>, two passes
+  out->enstrophy = 0.5 * h[11] / Pg;
+  out->dissipation = 0.5 * nu * h[12] / Pg;
   out->gamma_mean = NAN;
   out->gamma_std = NAN;
   out->nonfinite_count = (int64_t)h[10];

@@ -293,6 +293,9 @@ def test_bounded_wait_reports_timeout_and_context_recovers(kbc):
     with pytest.raises(lb.LBError) as e:
         lat.diagnostics()
     assert e.value.status == lb.LB_ERR_TIMEOUT
+    with pytest.raises(lb.LBError) as e:        # the state must be rewritten first
+        lat.step(1)
+    assert e.value.status == lb.LB_ERR_TIMEOUT
     lb.lb_set_wait_budget(lat.ctx, 2000000000, False)
     lb.lb_set_time(lat.ctx, 0)
     lat.set_populations(f0)
