@@ -8,9 +8,13 @@ update of the whole box. Other storage / scheme / batched variants are reported 
 "variants" in the same line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--scaling weak|strong] [--workload NAME]
 
-N > 1 (torchrun) runs independent replicas, one per GPU (weak scaling, no data-path
-collective); value = all ranks' lattice updates / max-over-ranks time.
+N > 1 (torchrun) runs, by default, independent replicas, one per GPU (weak scaling, no
+data-path collective); value = all ranks' lattice updates / max-over-ranks time. With
+--scaling strong the one box of the workload is split along z into one slab per rank, and the
+9 populations per face cross between neighbouring ranks every step (NCCL send/recv, overlapped
+with the interior planes' update); value = the box's lattice updates / max-over-ranks time.
 """
 from __future__ import annotations
 
@@ -335,6 +339,81 @@ def run_batch(w, steps, warmup, rank=0, world=1):
             "single_box_ms_per_step": single_ms / lat_steps, "diags": diags}
 
 
+def run_strong(w, steps, warmup, rank, world):
+    """Time `steps` steps of one box split along z into one slab per rank (strong scaling):
+    each step the boundary planes are stepped and their faces packed, the faces travel to the
+    neighbouring ranks (NCCL point-to-point, periodic ring) while the interior planes are
+    stepped, and the received faces are unpacked. No diagnostics in the timed region."""
+    import torch
+    from paper_1507_02518_gb300 import sharding
+    from paper_1507_02518_gb300 import slab as slabmod
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    n = w["n"]
+    z0, z1 = sharding.slab_bounds(n, rank, world)
+    rho, u = make_field(w)
+    u_dev = u if isinstance(u, torch.Tensor) else torch.from_numpy(u).cuda()
+    u_mine = u_dev[:, z0:z1].contiguous()
+    del rho, u, u_dev
+    torch.cuda.empty_cache()
+    s = slabmod.Slab(n, n, n, z0, z1 - z0, nu=w["nu"], storage=w["storage"],
+                     scheme=w["scheme"])
+    s.init_field(None, u_mine)
+    del u_mine
+    torch.cuda.empty_cache()
+    slabmod.step_distributed(s, rank, world, dist, warmup)
+    torch.cuda.synchronize()
+    barrier(world)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s.stream)
+    slabmod.step_distributed(s, rank, world, dist, steps)
+    b.record(s.stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    nz_local = z1 - z0
+    launches = steps * ((2 if nz_local > 1 else 1) + (1 if nz_local > 2 else 0) + 2)
+    s.close()
+    return {"P": n * n * nz_local, "P_box": n ** 3, "total_ms": ms, "launches": launches,
+            "planes": [z0, z1], "face_bytes": 9 * n * n * {"f64": 8, "f32": 4, "f16": 2}[
+                w["storage"]]}
+
+
+def main_strong(args, rank, world, local):
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1507_02518_gb300 import lb
+    lb.load()
+    w = parse_workload(args.workload)
+    if w["field"] == "batch":
+        raise SystemExit("strong scaling splits one box; a batch shards without exchange")
+    barrier(world)
+    with ClockSampler(local) as clk:
+        res = run_strong(w, args.steps, args.warmup, rank, world)
+    barrier(world)
+    ms_max = max_over_ranks(res["total_ms"], world)
+    value = res["P_box"] * args.steps / (ms_max / 1e3) / 1e6
+    out = None
+    if rank == 0:
+        peak, peak_kind = hbm_peak()
+        out = {
+            "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms_max / args.steps, 5), "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": w["storage"], "data": "synthetic",
+            "config": {"workload": workload_text(w) + " (no diagnostics in the timed region)",
+                       "box": [w["n"]] * 3, "storage": w["storage"], "scheme": w["scheme"],
+                       "parallelism": "%d slabs along z, face exchange per step" % world,
+                       "face_bytes_per_step_per_rank": 2 * res["face_bytes"],
+                       "l2": "populations %.2f GB per rank per step vs 129 MB L2 (no flush)"
+                             % (BYTES_PER_LUP[w["storage"]] * res["P"] / 1e9)},
+            "roofline": roofline(w["storage"], value / world, peak, peak_kind),
+            "gpu_launches": res["launches"], "clocks": clk.summary()}
+        print(json.dumps(out), flush=True)
+    barrier(world)
+    return out
+
+
 def run_e2e(w, steps):
     """Same metric through the public API with host buffers: H2D of the initial fields, the
     steps with diagnostics, D2H of the final rho and u, all inside the timed region."""
@@ -585,6 +664,8 @@ def parse_args(argv=None):
                         "list (names as for --workload, or batch<K>_<storage>_<scheme>)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--scaling", choices=["weak", "strong"], default="weak",
+                   help="weak: one box per rank (replicas); strong: one box split along z")
     a = p.parse_args(argv)
     if a.impl == "reference":
         a.steps = 3 if a.steps is None else a.steps
@@ -603,6 +684,8 @@ def main(argv=None):
     try:
         if args.impl == "reference":
             main_reference(args, rank, world)
+        elif args.scaling == "strong":
+            main_strong(args, rank, world, local)
         else:
             main_ours(args, rank, world, local)
     finally:

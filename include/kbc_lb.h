@@ -219,6 +219,13 @@ lb_status lb_stabilizer_gap(lb_ctx *ctx, lb_gap *out);
  * whatever the scheme and step parity. Synchronises. */
 lb_status lb_get_populations(lb_ctx *ctx, double *f, int on_device);
 
+/* The stabilizer gamma of every node from the last collision of the last lb_step call
+ * (eq:result21, or 2 / 1/beta in the LBGK / RLB modes; 2 where <dh|dh> fell under the guard;
+ * FP32, caller-owned gamma[P], node order). An FP32-arithmetic collision takes the value of
+ * its FP64 re-evaluation where its <dh|dh> fell under 1e-9. LB_ERR_INVALID_ARG when no step
+ * has run since the state was set. Synchronises. */
+lb_status lb_get_gamma(lb_ctx *ctx, float *gamma, int on_device);
+
 /* Overwrite the state with canonical populations f[27][P] at the current time t (checkpoint
  * resume, test seeding). Values are rounded to the storage precision. Synchronises. */
 lb_status lb_set_populations(lb_ctx *ctx, const double *f, int on_device);
@@ -230,7 +237,23 @@ double lb_beta(const lb_ctx *ctx);
  * lb_set_populations). t >= 0. */
 lb_status lb_set_time(lb_ctx *ctx, int64_t t);
 
-/* Which step kernel runs. All of them produce bit-identical populations.
+/* Which step kernel runs. The one-node-per-thread kernels (direct, staged, persistent) give
+ * bit-identical populations, and so do the two-nodes-per-thread kernels (packed, rows) among
+ * themselves; the two families agree to FP32 round-off (the FP32x2 instructions round some
+ * operations differently from their scalar forms). FP64 storage runs the direct kernel.
+ *   LB_KERNEL_ROWS        two adjacent nodes per thread on packed FP32x2 instructions; a
+ *                         persistent grid walks tiles of whole rows (nx <= 256) or 256-node
+ *                         row segments (nx a multiple of 256), whose 27 source rows the
+ *                         bulk-copy engine stages in shared memory ahead of the collision
+ *                         (mbarrier pipeline, bounded waits). Needs LB_F32 / LB_F16, the
+ *                         product-form equilibrium, a natural-moment variant, nx even with
+ *                         nx * sizeof(stored value) % 16 == 0, and for nx <= 256 a tile of R
+ *                         rows (R dividing ny) with R * nx a multiple of 64 in [128, 256];
+ *                         else LB_ERR_UNSUPPORTED.
+ *   LB_KERNEL_ADJ         two adjacent nodes (x, x+1) per thread on packed FP32x2
+ *                         instructions, straight from global memory: the planes not shifted
+ *                         in x are one 32/64-bit access per plane. Needs LB_F32 / LB_F16, the
+ *                         product-form equilibrium, a natural-moment variant and an even nx.
  *   LB_KERNEL_PACKED      two nodes per thread, (x, x+32) of one row, the collision on
  *                         packed FP32x2 instructions; LB_F32 / LB_F16 only.
  *   LB_KERNEL_PERSISTENT  a persistent grid walks 128-node row segments, one thread per node,
@@ -242,13 +265,17 @@ lb_status lb_set_time(lb_ctx *ctx, int64_t t);
  *                         nx * sizeof(stored value) % 16 == 0 (else LB_ERR_UNSUPPORTED).
  *                         Staged and persistent run the natural-moment variants only.
  *   LB_KERNEL_DIRECT      one thread per node over a full grid (lb_set_block), any nx.
- *   LB_KERNEL_AUTO        (default) packed for FP32 arithmetic, direct for LB_F64. */
+ *   LB_KERNEL_AUTO        (default) for FP32 arithmetic adjacent pairs where that kernel
+ *                         applies (even nx, product form, natural moments), packed
+ *                         otherwise; direct for LB_F64. */
 enum {
   LB_KERNEL_AUTO = 0,
   LB_KERNEL_DIRECT = 1,
   LB_KERNEL_STAGED = 2,
   LB_KERNEL_PERSISTENT = 3,
-  LB_KERNEL_PACKED = 4
+  LB_KERNEL_PACKED = 4,
+  LB_KERNEL_ROWS = 5,
+  LB_KERNEL_ADJ = 6
 };
 lb_status lb_set_kernel(lb_ctx *ctx, int32_t kind);
 
@@ -295,6 +322,39 @@ lb_status lb_set_wait_budget(lb_ctx *ctx, uint64_t cycles, int32_t stall_copies)
  * LB_ERR_NONFINITE; lb_last_error(NULL) explains. */
 lb_status lb_diagnostics_noalloc(int32_t nx, int32_t ny, int32_t nz, double nu, const double *f,
                                  void *stream, lb_diag *out);
+
+/* ---------------------------------------------------------------- slabs of one box split along z
+ * One periodic box (eq:Egeneral's propagation wraps in x, y and z) split into slabs of whole
+ * z-planes, one per GPU (the multi-GPU form of a single box). A slab context holds planes
+ * z0 .. z0 + nz_local - 1 of the global nx x ny x nz box plus one halo plane on each side; the
+ * collision is local, and after each step the 9 populations that cross each face (v_z = +1
+ * through the top, v_z = -1 through the bottom) travel to the neighbouring slab: per face and
+ * step 9 nx ny stored values. The caller moves them (NCCL send/recv, a peer copy, or a device
+ * copy when the slabs share a GPU): the library packs them into contiguous face buffers and
+ * unpacks what the caller delivered. One step is
+ *   lb_slab_step_faces(ctx, record)   steps the two boundary planes and packs send_up /
+ *                                     send_down (enqueue the sends after this call),
+ *   lb_slab_step_interior(ctx)        steps the other planes (overlaps the transfer), t += 1,
+ *   lb_slab_unpack(ctx)               after recv_below / recv_above hold the neighbours'
+ *                                     send_up / send_down of the same step.
+ * The slab below the global plane 0 is the one holding plane nz - 1 (periodic); a single slab
+ * holding the whole box is its own neighbour on both sides. Everything is enqueued on the
+ * context's stream; nothing synchronises. lb_init_field, lb_set_populations,
+ * lb_get_populations, lb_moments and lb_get_gamma work on a slab context with the slab's own
+ * nx*ny*nz_local nodes (local z = global z - z0) once its step is complete; lb_step,
+ * lb_diagnostics, lb_spectrum, lb_stabilizer_gap and lb_presolve are whole-box calls
+ * (LB_ERR_INVALID_ARG / LB_ERR_UNSUPPORTED). lb_destroy releases it. */
+size_t lb_slab_required_bytes(const lb_config *global, int32_t nz_local);
+lb_status lb_slab_create(const lb_config *global, int32_t z0, int32_t nz_local, void *dev_buf,
+                         size_t bytes, void *stream, lb_ctx **out);
+/* Device addresses of the four face buffers (inside the context's buffer) and their size,
+ * 9 * nx * ny * sizeof(stored value) bytes each. Any pointer may be NULL. */
+lb_status lb_slab_faces(lb_ctx *ctx, void **send_up, void **send_down, void **recv_below,
+                        void **recv_above, size_t *face_bytes);
+/* record != 0: the collision records gamma and the guard count (lb_get_gamma). */
+lb_status lb_slab_step_faces(lb_ctx *ctx, int32_t record);
+lb_status lb_slab_step_interior(lb_ctx *ctx);
+lb_status lb_slab_unpack(lb_ctx *ctx);
 
 /* ---------------------------------------------------------------- batched ensemble
  * Many independent periodic boxes of uneven sizes and viscosities, stepped together: one

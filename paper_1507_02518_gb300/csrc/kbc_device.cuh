@@ -1,6 +1,6 @@
 // kbc_device.cuh -- device-side building blocks of the D3Q27 KBC step (sm_103a).
 //
-// Method: arXiv:1507.02518, Sec. KBC (collision listing, Table 1, eq:result21) with the
+// Method: arXiv:1507.02518, Sec. KBC (eq:Egeneral with eq:ksh-mirror, Table 1, eq:result21) with the
 // product-form equilibrium eq:entropic_eq and the natural moments eq:natmoments.
 //
 // Register-level design (one thread = one lattice node):
@@ -17,6 +17,7 @@
 #pragma once
 
 #include <cuda_fp16.h>
+#include <string.h>
 #include <stdint.h>
 
 #include <type_traits>
@@ -41,22 +42,39 @@ __host__ __device__ constexpr int opp(int i) { return 26 - i; }
 
 // ------------------------------------------------------------------ storage codecs
 // Each storage type S maps to an arithmetic type R and encodes the shift delta = f - W.
+// load/store give and take the shift itself (diagnostics, transfers, pre-solve). The step
+// kernels use load_raw/store_raw, whose unit is the collision's: the shift for FP64 and FP32,
+// and the shift relative to the weight, (f - W)/W, for FP16 (rel = true), so that no
+// per-population scaling sits between the stored halves and the collision (the collision
+// folds the weights into its constants).
 template <typename S> struct Codec;
 
 template <> struct Codec<double> {
   using R = double;
+  static constexpr bool rel = false;
   template <int I> __device__ static __forceinline__ R load(const double* p) { return *p; }
   template <int I> __device__ static __forceinline__ R load_ro(const double* p) { return __ldg(p); }
   template <int I> __device__ static __forceinline__ void store(double* p, R d) { *p = d; }
+  template <int I> __device__ static __forceinline__ R load_raw(const double* p) { return *p; }
+  template <int I> __device__ static __forceinline__ R load_raw_ro(const double* p) {
+    return __ldg(p);
+  }
+  template <int I> __device__ static __forceinline__ void store_raw(double* p, R d) { *p = d; }
   __host__ __device__ static double to_delta(double s, int) { return s; }
   __host__ __device__ static double from_delta(double d, int) { return d; }
 };
 
 template <> struct Codec<float> {
   using R = float;
+  static constexpr bool rel = false;
   template <int I> __device__ static __forceinline__ R load(const float* p) { return *p; }
   template <int I> __device__ static __forceinline__ R load_ro(const float* p) { return __ldg(p); }
   template <int I> __device__ static __forceinline__ void store(float* p, R d) { *p = d; }
+  template <int I> __device__ static __forceinline__ R load_raw(const float* p) { return *p; }
+  template <int I> __device__ static __forceinline__ R load_raw_ro(const float* p) {
+    return __ldg(p);
+  }
+  template <int I> __device__ static __forceinline__ void store_raw(float* p, R d) { *p = d; }
   __device__ static double to_delta(float s, int) { return (double)s; }
   __device__ static float from_delta(double d, int) { return (float)d; }
 };
@@ -65,14 +83,24 @@ template <> struct Codec<float> {
 // relative to W_i keeps every direction clear of the half subnormal range.
 template <> struct Codec<uint16_t> {
   using R = float;
+  static constexpr bool rel = true;
   template <int I> __device__ static __forceinline__ R load(const uint16_t* p) {
-    return (float)wgt(I) * __half2float(__ushort_as_half(*p));
+    return __fmul_rn((float)wgt(I), __half2float(__ushort_as_half(*p)));
   }
   template <int I> __device__ static __forceinline__ R load_ro(const uint16_t* p) {
-    return (float)wgt(I) * __half2float(__ushort_as_half(__ldg(p)));
+    return __fmul_rn((float)wgt(I), __half2float(__ushort_as_half(__ldg(p))));
   }
   template <int I> __device__ static __forceinline__ void store(uint16_t* p, R d) {
-    *p = __half_as_ushort(__float2half_rn(d * (float)inv_wgt(I)));
+    *p = __half_as_ushort(__float2half_rn(__fmul_rn(d, (float)inv_wgt(I))));
+  }
+  template <int I> __device__ static __forceinline__ R load_raw(const uint16_t* p) {
+    return __half2float(__ushort_as_half(*p));
+  }
+  template <int I> __device__ static __forceinline__ R load_raw_ro(const uint16_t* p) {
+    return __half2float(__ushort_as_half(__ldg(p)));
+  }
+  template <int I> __device__ static __forceinline__ void store_raw(uint16_t* p, R d) {
+    *p = __half_as_ushort(__float2half_rn(d));
   }
   __device__ static double to_delta(uint16_t s, int i) {
     return wgt(i) * (double)__half2float(__ushort_as_half(s));
@@ -82,16 +110,17 @@ template <> struct Codec<uint16_t> {
   }
 };
 
-// Two values of one plane (nodes xa and xb) at a time, for the packed kernel.
+// Two values of one plane (nodes a and b) at a time in the collision's unit (load_raw /
+// store_raw above), for the packed kernels.
 template <typename S> struct Codec2;
 template <> struct Codec2<float> {
   template <int I, bool RO>
   __device__ static __forceinline__ float2 load(const float* pa, const float* pb) {
     return RO ? make_float2(__ldg(pa), __ldg(pb)) : make_float2(*pa, *pb);
   }
-  template <int I> __device__ static __forceinline__ void store(float* pa, float* pb, bool vb,
-                                                              float2 v) {
-    *pa = v.x;
+  template <int I> __device__ static __forceinline__ void store(float* pa, float* pb, bool va,
+                                                              bool vb, float2 v) {
+    if (va) *pa = v.x;
     if (vb) *pb = v.y;
   }
 };
@@ -99,22 +128,84 @@ template <> struct Codec2<uint16_t> {
   template <int I, bool RO>
   __device__ static __forceinline__ float2 load(const uint16_t* pa, const uint16_t* pb) {
     const uint16_t a = RO ? __ldg(pa) : *pa, b = RO ? __ldg(pb) : *pb;
-    const float2 h = __half22float2(__halves2half2(__ushort_as_half(a), __ushort_as_half(b)));
-    return __fmul2_rn(make_float2((float)wgt(I), (float)wgt(I)), h);
+    return __half22float2(__halves2half2(__ushort_as_half(a), __ushort_as_half(b)));
   }
   template <int I> __device__ static __forceinline__ void store(uint16_t* pa, uint16_t* pb,
-                                                              bool vb, float2 v) {
-    const float iw = (float)inv_wgt(I);
-    const __half2 h = __float22half2_rn(__fmul2_rn(make_float2(iw, iw), v));
-    *pa = __half_as_ushort(__low2half(h));
+                                                              bool va, bool vb, float2 v) {
+    const __half2 h = __float22half2_rn(v);
+    if (va) *pa = __half_as_ushort(__low2half(h));
     if (vb) *pb = __half_as_ushort(__high2half(h));
   }
+};
+
+// Two adjacent nodes (x, x + 1) of one plane in the collision's unit, for the kernels that
+// give a thread two neighbouring nodes of a row: v0, vl and vr point at the values of nodes x,
+// x - 1 and x + 2 (row neighbours, periodic wrap already applied); SX selects the pair read,
+// nodes (x + SX, x + 1 + SX). The unshifted pair is one 32-bit (FP16) or 64-bit (FP32) access
+// (x even, rows of even length); a shifted pair is two scalar accesses. RO: read-only path.
+template <typename S> struct PairIO;
+template <> struct PairIO<uint16_t> {
+  template <bool RO> __device__ static __forceinline__ uint16_t ld1(const uint16_t* p) {
+    return RO ? __ldg(p) : *p;
+  }
+  template <int SX, bool RO>
+  __device__ static __forceinline__ float2 get(const uint16_t* v0, const uint16_t* vl,
+                                               const uint16_t* vr) {
+    if constexpr (SX == 0) {
+      const unsigned int w = RO ? __ldg(reinterpret_cast<const unsigned int*>(v0))
+                                : *reinterpret_cast<const unsigned int*>(v0);
+      __half2 h;
+      memcpy(&h, &w, sizeof h);
+      return __half22float2(h);
+    } else if constexpr (SX < 0) {
+      return __half22float2(
+          __halves2half2(__ushort_as_half(ld1<RO>(vl)), __ushort_as_half(ld1<RO>(v0))));
+    } else {
+      return __half22float2(
+          __halves2half2(__ushort_as_half(ld1<RO>(v0 + 1)), __ushort_as_half(ld1<RO>(vr))));
+    }
+  }
+  __device__ static __forceinline__ void put2(uint16_t* p, float2 v) {
+    *reinterpret_cast<__half2*>(p) = __float22half2_rn(v);
+  }
+  __device__ static __forceinline__ void put1(uint16_t* p, float v) {
+    *p = __half_as_ushort(__float2half_rn(v));
+  }
+};
+template <> struct PairIO<float> {
+  template <bool RO> __device__ static __forceinline__ float ld1(const float* p) {
+    return RO ? __ldg(p) : *p;
+  }
+  template <int SX, bool RO>
+  __device__ static __forceinline__ float2 get(const float* v0, const float* vl,
+                                               const float* vr) {
+    if constexpr (SX == 0) {
+      return RO ? __ldg(reinterpret_cast<const float2*>(v0))
+                : *reinterpret_cast<const float2*>(v0);
+    } else if constexpr (SX < 0) {
+      return make_float2(ld1<RO>(vl), ld1<RO>(v0));
+    } else {
+      return make_float2(ld1<RO>(v0 + 1), ld1<RO>(vr));
+    }
+  }
+  __device__ static __forceinline__ void put2(float* p, float2 v) {
+    *reinterpret_cast<float2*>(p) = v;
+  }
+  __device__ static __forceinline__ void put1(float* p, float v) { *p = v; }
 };
 
 // guard on <dh|dh> (the paper is silent when it vanishes; gamma falls back to 2, LBGK)
 template <typename R> struct Guard;
 template <> struct Guard<double> { static constexpr double den = 1e-300; };
 template <> struct Guard<float> { static constexpr float den = 1e-30f; };
+
+// An FP32 collision whose <dh|dh> falls under kDenFp64 is not used: the lane is flagged
+// (*fp64 bit k), its populations are not stored, and the step kernel collides that node again
+// in FP64 from its stored inputs (fp64_node_update), with the FP64 guard of the oracle. Below
+// kDenFp64, dh is within about a thousand FP32 round-offs of the shifts it is the difference
+// of, so an FP32 <dh|dh> -- and the ratio of eq:result21 -- would carry that error; an
+// accurate denominator needs dh, and so the node's moments and equilibrium, in FP64.
+constexpr float kDenFp64 = 1e-9f;
 
 enum { GAMMA_ESTIMATE = 0, GAMMA_LBGK = 1, GAMMA_RLB = 2, GAMMA_EXACT = 3 };
 
@@ -174,6 +265,7 @@ template <> struct Ar<float> {
   static __device__ __forceinline__ float sqrt_fast(float a) {
     return __fmul_rn(a, rsqrt_approx(a));
   }
+  static __device__ __forceinline__ float rcp_fast(float a) { return rcp_approx(a); }
   static __device__ __forceinline__ float lane(float a, int) { return a; }
   static __device__ __forceinline__ void set_lane(float& a, int, float v) { a = v; }
 };
@@ -196,6 +288,9 @@ template <> struct Ar<float2> {
   }
   static __device__ __forceinline__ float2 sqrt_fast(float2 a) {
     return __fmul2_rn(a, make_float2(rsqrt_approx(a.x), rsqrt_approx(a.y)));
+  }
+  static __device__ __forceinline__ float2 rcp_fast(float2 a) {
+    return make_float2(rcp_approx(a.x), rcp_approx(a.y));
   }
   static __device__ __forceinline__ float lane(float2 a, int k) { return k ? a.y : a.x; }
   static __device__ __forceinline__ void set_lane(float2& a, int k, float v) {
@@ -284,9 +379,12 @@ __device__ __noinline__ T newton_gamma(const T (&dh)[27], const T (&av)[27], con
   return g;
 }
 
-// One KBC collision on the shifted populations d[i] = f_i - W_i, in place (collision
-// listing of Sec. KBC); R holds one node (float, double) or two (float2). Returns gamma;
-// bit k of *guarded is set when lane k's <dh|dh> fell under the guard.
+// One KBC collision on the shifted populations d[i] = f_i - W_i, in place: the post-collision
+// state of eq:Egeneral with the mirror state eq:ksh-mirror, f' = f - beta (2 ds + gamma dh),
+// ds = s - s_eq by Table 1, dh = f - f_eq - ds, gamma by eq:result21 (Sec. KBC); R holds one
+// node (float, double) or two (float2). Returns gamma; bit k of *guarded is set when lane k's
+// <dh|dh> fell under the guard. fp64 (FP32 arithmetic only): if given, bit k is set when
+// lane k's <dh|dh> fell under kDenFp64 (its outputs are then to be replaced in FP64).
 // EXACT (one node per thread only): gamma is the root of eq:result1 found by newton_gamma()
 // from the estimate; *gamma_est receives the estimate and *newton the solver's status.
 // POLY: the equilibrium is the second-order polynomial eq:polynomial2 instead of the product
@@ -294,7 +392,7 @@ __device__ __noinline__ T newton_gamma(const T (&dh)[27], const T (&av)[27], con
 template <typename R, bool CENTRAL = false, bool EXACT = false, bool POLY = false>
 __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, int* guarded,
                                      typename Ar<R>::Scalar* gamma_est = nullptr,
-                                     int* newton = nullptr) {
+                                     int* newton = nullptr, int* fp64 = nullptr) {
   using O = Ar<R>;
   using T = typename O::Scalar;
   static_assert(!(EXACT && POLY), "the exact stabilizer is built for the product form only");
@@ -334,14 +432,14 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, int* g
   const R D120 = zsum(Y12);
   const R D210 = zsum(Y21);
 
-  // ---- conserved quantities (listing step 1); sum W = 1, sum W v = 0
+  // ---- conserved quantities rho, u (eq:natmoments); sum W = 1, sum W v = 0
   const R one = O::c(1.0), three = O::c(3.0);
   const R drho = D000;
   const R rho = O::add(one, drho);
   const R ir = O::div_fast(one, rho);
   const R ux = O::mul(D100, ir), uy = O::mul(D010, ir), uz = O::mul(D001, ir);
 
-  // ---- per-axis equilibrium factors (listing step 2): e = R - 1 = 3u^2 / (1 + R)
+  // ---- per-axis factors of the equilibrium eq:entropic_eq: e = R - 1 = 3u^2 / (1 + R)
   // FP32: 3u^2/(1 + R) avoids the cancellation of R - 1 at small u. FP64: R - 1 directly
   // (exact subtraction, absolute error ~1e-16, far below what the populations resolve),
   // which saves a division on GB300's narrow FP64 pipe.
@@ -374,7 +472,7 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, int* g
     m3z = O::fma(c23, ez, c13);
   }
 
-  // ---- rho-scaled moment deviations rho (M - M_eq) (listing steps 3-4)
+  // ---- rho-scaled moment deviations rho (M - M_eq), the inputs of Table 1 for ds = s - s_eq
   const R nrc23 = O::neg(O::mul(rho, c23));
   const R nd3 = O::mul(drho, O::c(-1.0 / 3.0));
   const R A200 = O::fma(nrc23, ex, O::add(D200, nd3));
@@ -492,7 +590,8 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, int* g
       POLY ? O::mul(O::c(-1.5), O::fma(ux, ux, O::fma(uy, uy, O::mul(uz, uz)))) : O::c(0.0);
 
   // ---- dh, the two entropic products, and the part of the relaxation known before gamma
-  // (listing steps 5-6): d <- d - 2 beta ds, dh kept for the gamma-dependent part
+  // (Sec. KBC: dh = f - f_eq - ds; <X|Y> = sum X_i Y_i / f_eq_i): d <- d - 2 beta ds, dh kept
+  // for the gamma-dependent part
   const R nb2 = O::bc(-prec<T>(cp.two_beta, cp.two_betaf));
   R dh[27];
   // a_i = dh_i - (2 beta - 1) ds_i, kept for the exact stabilizer only
@@ -620,7 +719,7 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, int* g
     }
   }
 
-  // ---- stabilizer (eq:result21) and the rest of the relaxation (listing step 7)
+  // ---- stabilizer (eq:result21) and the rest of the relaxation f' = f - beta(2 ds + gamma dh)
   const T ib = prec<T>(cp.inv_beta, cp.inv_betaf);
   R gamma = O::c(0.0);
   int gmask = 0;
@@ -632,6 +731,10 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, int* g
       gk = T(2);
     } else if (cp.gamma_mode == GAMMA_RLB) {
       gk = ib;
+    } else if (std::is_same<T, float>::value && !EXACT && fp64 && dk < T(kDenFp64) &&
+               dk == dk) {
+      gk = T(2);  // replaced by the FP64 collision of this node
+      *fp64 |= 1 << k;
     } else if (dk > Guard<T>::den) {
       gk = Ar<T>::fma(-Ar<T>::sub(T(2), ib), Ar<T>::div_fast(nk, dk), ib);
     } else if (dk == dk) {
@@ -657,6 +760,287 @@ __device__ __forceinline__ R collide(R (&d)[27], const CollideParams& cp, int* g
   for (int i = 0; i < 27; ++i) d[i] = O::fma(nbg, dh[i], d[i]);
   return gamma;
 }
+
+// ------------------------------------------------------------------ lean FP32 collision
+// The collision of collide() for the product-form equilibrium and the natural-moment shear
+// parts, in FP32 arithmetic (R = float or float2), arranged for the fewest FP32 operations per
+// node (every FP32 step kernel of these variants runs it):
+//   * REL (FP16 storage): the data are h_i = (f_i - W_i) / W_i. Each moment stage weights the
+//     velocities -1, 0, +1 as 1 : 4 : 1 (that is 6 W_v), so the moments come out 216 times
+//     their value; that factor and the 1/W_i of the outputs sit in the constants of Table 1's
+//     class values, and dh/W = h - G - ds/W needs no weight per population;
+//   * the entropic weights (W_i/f_eq_i for REL, 1/f_eq_i otherwise) are products of one MUFU
+//     reciprocal per axis and velocity component;
+//   * the q part's switch multiplies three class constants, not the seven third moments;
+//   * 3u^2 reuses 3u, and the first term of each entropic sum is a product, not an FMA on 0.
+template <typename R, bool REL>
+__device__ __forceinline__ R collide_lean(R (&d)[27], const CollideParams& cp, int* guarded,
+                                          int* fp64) {
+  using O = Ar<R>;
+  using T = float;
+  static_assert(std::is_same<typename O::Scalar, float>::value, "FP32 arithmetic only");
+  const R one = O::c(1.0), three = O::c(3.0);
+  // ---- moments (eq:natmoments) by a factorised x -> y -> z reduction; REL weights 1 : 4 : 1
+  auto stage0 = [&](R m, R z, R p) {
+    const R s = O::add(p, m);
+    if constexpr (REL) return O::fma(O::c(4.0), z, s);
+    else return O::add(s, z);
+  };
+  R X0[9], X1[9], X2[9];
+#pragma unroll
+  for (int r = 0; r < 9; ++r) {
+    const R m = d[3 * r + 0], z = d[3 * r + 1], p = d[3 * r + 2];
+    X2[r] = O::add(p, m);
+    X1[r] = O::sub(p, m);
+    X0[r] = stage0(m, z, p);
+  }
+  auto ystage = [&](const R (&X)[9], R (&Y0)[3], R (&Y1)[3], R (&Y2)[3]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const R m = X[3 * c + 0], z = X[3 * c + 1], p = X[3 * c + 2];
+      Y2[c] = O::add(p, m);
+      Y1[c] = O::sub(p, m);
+      Y0[c] = stage0(m, z, p);
+    }
+  };
+  R Y00[3], Y01[3], Y02[3], Y10[3], Y11[3], Y12[3], Y20[3], Y21[3], Y22[3];
+  ystage(X0, Y00, Y01, Y02);
+  ystage(X1, Y10, Y11, Y12);
+  ystage(X2, Y20, Y21, Y22);
+  (void)Y22;
+  auto zsum = [&](const R (&Y)[3]) { return stage0(Y[0], Y[1], Y[2]); };
+  // E_pqr = D_pqr / K: the moment sums of the data, K = 1/216 for REL
+  const R E000 = zsum(Y00), E001 = O::sub(Y00[2], Y00[0]), E002 = O::add(Y00[2], Y00[0]);
+  const R E100 = zsum(Y10), E101 = O::sub(Y10[2], Y10[0]), E102 = O::add(Y10[2], Y10[0]);
+  const R E010 = zsum(Y01), E011 = O::sub(Y01[2], Y01[0]), E012 = O::add(Y01[2], Y01[0]);
+  const R E200 = zsum(Y20), E201 = O::sub(Y20[2], Y20[0]);
+  const R E020 = zsum(Y02), E021 = O::sub(Y02[2], Y02[0]);
+  const R E110 = zsum(Y11), E111 = O::sub(Y11[2], Y11[0]);
+  const R E120 = zsum(Y12);
+  const R E210 = zsum(Y21);
+  constexpr double K = REL ? 1.0 / 216.0 : 1.0;
+
+  // ---- conserved quantities rho, u; kir = K / rho
+  R drho, rho, kir;
+  if constexpr (REL) {
+    drho = O::mul(E000, O::c(K));
+    rho = O::add(one, drho);
+    kir = O::rcp_fast(O::add(O::c(216.0), E000));
+  } else {
+    drho = E000;
+    rho = O::add(one, drho);
+    kir = O::rcp_fast(rho);
+  }
+  const R ux = O::mul(E100, kir), uy = O::mul(E010, kir), uz = O::mul(E001, kir);
+
+  // ---- per-axis factors of eq:entropic_eq: e = R - 1 = 3u^2 / (1 + R), R = sqrt(1 + 3u^2)
+  R ux3, uy3, uz3, ex, ey, ez;
+  auto axis = [&](R u, R& u3, R& e) {
+    u3 = O::mul(three, u);
+    const R uu3 = O::mul(u3, u);
+    const R Rr = O::sqrt_fast(O::add(one, uu3));
+    e = O::mul(uu3, O::rcp_fast(O::add(one, Rr)));
+  };
+  axis(ux, ux3, ex);
+  axis(uy, uy3, ey);
+  axis(uz, uz3, ez);
+  const R c23 = O::c(2.0 / 3.0), c13 = O::c(1.0 / 3.0);
+  const R m3x = O::fma(c23, ex, c13), m3y = O::fma(c23, ey, c13), m3z = O::fma(c23, ez, c13);
+
+  // ---- rho (M - M_eq): second moments at their value, the others at 1/K of it
+  const R nrc23 = O::mul(rho, O::c(-2.0 / 3.0));
+  const R nd3 = O::mul(drho, O::c(-1.0 / 3.0));
+  auto second = [&](R E, R e) {
+    if constexpr (REL) return O::fma(nrc23, e, O::fma(E, O::c(K), nd3));
+    else return O::fma(nrc23, e, O::add(E, nd3));
+  };
+  const R A200 = second(E200, ex), A020 = second(E020, ey), A002 = second(E002, ez);
+  const R ANxz = O::sub(A200, A002), ANyz = O::sub(A020, A002);
+  const R ATfull = O::add(O::add(A200, A020), A002);
+  const R AT = cp.with_t ? ATfull : O::c(0.0);
+  const R nE100 = O::neg(E100), nE010 = O::neg(E010), nE001 = O::neg(E001);
+  const R APxy = O::fma(nE100, uy, E110), APxz = O::fma(nE100, uz, E101);
+  const R APyz = O::fma(nE010, uz, E011);
+  const R RQxyy = O::fma(nE100, m3y, E120), RQxzz = O::fma(nE100, m3z, E102);
+  const R RQxxy = O::fma(nE010, m3x, E210), RQyzz = O::fma(nE010, m3z, E012);
+  const R RQxxz = O::fma(nE001, m3x, E201), RQyyz = O::fma(nE001, m3y, E021);
+  const R RQxyz = O::fma(O::mul(nE100, uy), uz, E111);
+
+  // ---- Table 1 class values of ds in the data's unit (REL: ds_i / W_i)
+  constexpr double wR = REL ? 27.0 / 8.0 : 1.0, wF = REL ? 13.5 : 1.0;
+  constexpr double wE = REL ? 54.0 : 1.0, wC = REL ? 216.0 : 1.0;
+  const T qf = cp.with_q ? 1.0f : 0.0f;
+  const R cG = O::bc(qf * (float)(K * wF / 2.0));
+  const R cQ4 = O::bc(qf * (float)(K * wE / 4.0));
+  const R cQ8 = O::bc(qf * (float)(K * wC / 8.0));
+  const R s0 = O::mul(AT, O::c(-wR));
+  const R cF = O::c(wF / 6.0);
+  const R Fx = O::mul(O::add(O::sub(O::add(ANxz, ANxz), ANyz), AT), cF);
+  const R Fy = O::mul(O::add(O::sub(O::add(ANyz, ANyz), ANxz), AT), cF);
+  const R Fz = O::mul(O::sub(O::sub(AT, ANxz), ANyz), cF);
+  const R Gx = O::mul(O::add(RQxyy, RQxzz), cG);
+  const R Gy = O::mul(O::add(RQxxy, RQyzz), cG);
+  const R Gz = O::mul(O::add(RQxxz, RQyyz), cG);
+  const R cP = O::c(K * wE / 4.0);
+  const R Pxy4 = O::mul(APxy, cP), Pxz4 = O::mul(APxz, cP), Pyz4 = O::mul(APyz, cP);
+  const R Qxxy4 = O::mul(RQxxy, cQ4), Qxyy4 = O::mul(RQxyy, cQ4);
+  const R Qxxz4 = O::mul(RQxxz, cQ4), Qxzz4 = O::mul(RQxzz, cQ4);
+  const R Qyyz4 = O::mul(RQyyz, cQ4), Qyzz4 = O::mul(RQyzz, cQ4);
+  const R Qxyz8 = O::mul(RQxyz, cQ8);
+  auto sg = [](int s, R v) { return s > 0 ? v : O::neg(v); };
+  auto edge = [&](int sp, R P4, int s1, R Q1, int s2, R Q2) {
+    return O::add(O::add(sg(sp, P4), sg(s1, Q1)), sg(s2, Q2));
+  };
+  auto ds_of = [&](int a, int b, int c) -> R {
+    const int nnz = (a != 0) + (b != 0) + (c != 0);
+    if (nnz == 0) return s0;
+    if (nnz == 1) {
+      if (a != 0) return a > 0 ? O::sub(Fx, Gx) : O::add(Fx, Gx);
+      if (b != 0) return b > 0 ? O::sub(Fy, Gy) : O::add(Fy, Gy);
+      return c > 0 ? O::sub(Fz, Gz) : O::add(Fz, Gz);
+    }
+    if (nnz == 2) {
+      if (c == 0) return edge(a * b, Pxy4, b, Qxxy4, a, Qxyy4);
+      if (b == 0) return edge(a * c, Pxz4, c, Qxxz4, a, Qxzz4);
+      return edge(b * c, Pyz4, c, Qyyz4, b, Qyzz4);
+    }
+    return sg(a * b * c, Qxyz8);
+  };
+
+  // ---- equilibrium: f_eq_i / W_i = X_a Y_b Z_c with X_a = 1 + gx_a (carrying rho),
+  // Y_b = 1 + fy_b, Z_c = 1 + fz_c, e_0 = -e, e_{+-1} = 2e +- 3u
+  const R tex = O::add(ex, ex), tey = O::add(ey, ey), tez = O::add(ez, ez);
+  R gx[3], fy[3], fz[3];
+  gx[0] = O::fma(rho, O::sub(tex, ux3), drho);
+  gx[1] = O::fma(O::neg(rho), ex, drho);
+  gx[2] = O::fma(rho, O::add(tex, ux3), drho);
+  fy[0] = O::sub(tey, uy3);
+  fy[1] = O::neg(ey);
+  fy[2] = O::add(tey, uy3);
+  fz[0] = O::sub(tez, uz3);
+  fz[1] = O::neg(ez);
+  fz[2] = O::add(tez, uz3);
+  // entropic weights per axis: REL W_a / X_a, otherwise 1 / (W_a X_a)
+  R wx[3], wy[3], wz[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double Wa = a == 1 ? 2.0 / 3.0 : 1.0 / 6.0;
+    const R cw = O::c(REL ? 1.0 / Wa : Wa);
+    wx[a] = O::rcp_fast(O::fma(cw, gx[a], cw));
+    wy[a] = O::rcp_fast(O::fma(cw, fy[a], cw));
+    wz[a] = O::rcp_fast(O::fma(cw, fz[a], cw));
+  }
+  // X_a Y_b - 1 for the 9 (a, b) pairs, without cancellation
+  R Pab[9];
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Pab[a + 3 * b] = O::fma(gx[a], fy[b], O::add(gx[a], fy[b]));
+
+  // ---- dh (Sec. KBC: dh = f - f_eq - ds), the entropic products <ds|dh>, <dh|dh>, and the
+  // part of f' = f - beta (2 ds + gamma dh) known before gamma
+  const R nb2 = O::bc(-cp.two_betaf);
+  R dh[27];
+  R num, den;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    R cn, cd;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      R rn, rd;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int i = a + 3 * b + 9 * c;
+        const R P = Pab[a + 3 * b];
+        const R G = O::fma(P, fz[c], O::add(P, fz[c]));  // X_a Y_b Z_c - 1
+        const R dsi = ds_of(a - 1, b - 1, c - 1);
+        R dhi;
+        if constexpr (REL) dhi = O::sub(O::sub(d[i], G), dsi);
+        else dhi = O::sub(O::fma(O::c(-wgt(i)), G, d[i]), dsi);
+        const R t1 = O::mul(wx[a], dhi);
+        if (a == 0) {
+          rn = O::mul(t1, dsi);
+          rd = O::mul(t1, dhi);
+        } else {
+          rn = O::fma(t1, dsi, rn);
+          rd = O::fma(t1, dhi, rd);
+        }
+        dh[i] = dhi;
+        d[i] = O::fma(nb2, dsi, d[i]);
+      }
+      if (b == 0) {
+        cn = O::mul(wy[b], rn);
+        cd = O::mul(wy[b], rd);
+      } else {
+        cn = O::fma(wy[b], rn, cn);
+        cd = O::fma(wy[b], rd, cd);
+      }
+    }
+    if (c == 0) {
+      num = O::mul(wz[c], cn);
+      den = O::mul(wz[c], cd);
+    } else {
+      num = O::fma(wz[c], cn, num);
+      den = O::fma(wz[c], cd, den);
+    }
+  }
+
+  // ---- stabilizer (eq:result21) and the rest of the relaxation
+  const T ib = cp.inv_betaf;
+  R gamma = O::c(0.0);
+  int gmask = 0;
+#pragma unroll
+  for (int k = 0; k < O::lanes; ++k) {
+    const T nk = O::lane(num, k), dk = O::lane(den, k);
+    T gk;
+    if (cp.gamma_mode == GAMMA_LBGK) {
+      gk = T(2);
+    } else if (cp.gamma_mode == GAMMA_RLB) {
+      gk = ib;
+    } else if (fp64 && dk < kDenFp64 && dk == dk) {
+      gk = T(2);  // replaced by the FP64 collision of this node
+      *fp64 |= 1 << k;
+    } else if (dk > Guard<T>::den) {
+      gk = Ar<T>::fma(-Ar<T>::sub(T(2), ib), Ar<T>::div_fast(nk, dk), ib);
+    } else if (dk == dk) {
+      gk = T(2);
+      gmask |= 1 << k;
+    } else {
+      gk = dk;  // NaN propagates to the populations and to the diagnostics
+    }
+    O::set_lane(gamma, k, gk);
+  }
+  *guarded = gmask;
+  const R nbg = O::mul(O::bc(-cp.betaf), gamma);
+#pragma unroll
+  for (int i = 0; i < 27; ++i) d[i] = O::fma(nbg, dh[i], d[i]);
+  return gamma;
+}
+
+// The collision of a step kernel on data in the storage's collision unit (REL: relative to
+// W_i, the FP16 codec): the lean form for FP32 arithmetic, product-form equilibrium and
+// natural moments; collide() otherwise.
+template <typename R, bool CENTRAL, bool EXACT, bool POLY, bool REL>
+__device__ __forceinline__ R collide_step(R (&d)[27], const CollideParams& cp, int* guarded,
+                                          int* fp64) {
+  using O = Ar<R>;
+  using T = typename O::Scalar;
+  if constexpr (!CENTRAL && !EXACT && !POLY && std::is_same<T, float>::value) {
+    return collide_lean<R, REL>(d, cp, guarded, fp64);
+  } else {
+    if constexpr (REL) {
+#pragma unroll
+      for (int i = 0; i < 27; ++i) d[i] = O::mul(O::c(wgt(i)), d[i]);
+    }
+    const R g = collide<R, CENTRAL, EXACT, POLY>(d, cp, guarded, nullptr, nullptr, fp64);
+    if constexpr (REL) {
+#pragma unroll
+      for (int i = 0; i < 27; ++i) d[i] = O::mul(O::c(inv_wgt(i)), d[i]);
+    }
+    return g;
+  }
+}
+
 
 // Equilibrium shift f_eq_i(rho, u) - W_i by the same per-axis closed form, in the precision T
 // of the arguments (FP64 for initialisation, the collision precision for the pre-solve).
@@ -694,6 +1078,7 @@ enum { MODE_PULL = 0, MODE_AA_EVEN = 1, MODE_AA_ODD = 2 };
 struct Geo {
   uint32_t nx, ny, nz, nxy;
   uint64_t P;
+  uint32_t zb, ze;  // the step kernels update the planes zb <= z < ze (all: 0, nz)
 };
 
 // in-plane offsets of the 3x3x3 neighbourhood of (x, y, z) on the periodic box
@@ -745,6 +1130,37 @@ template <int N> struct Unroll<N, N> {
   template <typename F> __device__ __forceinline__ static void run(F&&) {}
 };
 
+// FP64 collision of one node whose FP32 <dh|dh> fell under kDenFp64: loads the node's inputs
+// where the step's pattern keeps them (the step stores a node's slots only after its
+// collision, and has not stored this node), collides them in FP64 (collide<double>, with the
+// oracle's guard) and stores the outputs in the storage type. Returns gamma; *guarded is set
+// when <dh|dh> fell under the FP64 guard. Called outside the FP32 collision, with little live,
+// so that the call does not weigh on the FP32 kernels' registers.
+template <typename S, int MODE, bool CENTRAL, bool POLY>
+__device__ __noinline__ float fp64_node_update(const S* src, S* dst, Geo g, uint32_t x,
+                                               uint32_t y, uint32_t z, CollideParams cp,
+                                               int* guarded) {
+  using C = Codec<S>;
+  using Pat = Pattern<MODE>;
+  Nbr nb;
+  nb.init(g, x, y, z);
+  double d[27];
+  Unroll<0, 27>::run([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    d[I] = C::to_delta(
+        src[(uint64_t)Pat::load_plane(I) * g.P + nb.template at<I, Pat::load_shift>()], I);
+  });
+  int gd = 0;
+  const double gam = collide<double, CENTRAL, false, POLY>(d, cp, &gd);
+  Unroll<0, 27>::run([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    dst[(uint64_t)Pat::store_plane(I) * g.P + nb.template at<I, Pat::store_shift>()] =
+        C::from_delta(d[I], I);
+  });
+  *guarded = gd;
+  return (float)gam;
+}
+
 // ------------------------------------------------------------------ the fused node update
 // Loads f(x, t) of node (x, y, z) by the pattern of MODE, collides, stores f'(x) where
 // f(t+1) expects it. src and dst are the same buffer in the AA modes.
@@ -763,18 +1179,23 @@ __device__ __forceinline__ void node_update(const S* src, S* dst, const Geo& g, 
     constexpr int I = decltype(ic)::value;
     const S* p = src + (uint64_t)Pat::load_plane(I) * g.P + nb.template at<I, Pat::load_shift>();
     if constexpr (MODE == MODE_PULL) {
-      d[I] = C::template load_ro<I>(p);
+      d[I] = C::template load_raw_ro<I>(p);
     } else {
-      d[I] = C::template load<I>(p);
+      d[I] = C::template load_raw<I>(p);
     }
   });
-  int guarded;
-  const R gamma = collide<R, CENTRAL, EXACT, POLY>(d, cp, &guarded);
-  Unroll<0, 27>::run([&](auto ic) {
-    constexpr int I = decltype(ic)::value;
-    S* p = dst + (uint64_t)Pat::store_plane(I) * g.P + nb.template at<I, Pat::store_shift>();
-    C::template store<I>(p, d[I]);
-  });
+  int guarded, fp64 = 0;
+  R gamma = collide_step<R, CENTRAL, EXACT, POLY, C::rel>(
+      d, cp, &guarded, std::is_same<R, float>::value ? &fp64 : nullptr);
+  if (!fp64) {
+    Unroll<0, 27>::run([&](auto ic) {
+      constexpr int I = decltype(ic)::value;
+      S* p = dst + (uint64_t)Pat::store_plane(I) * g.P + nb.template at<I, Pat::store_shift>();
+      C::template store_raw<I>(p, d[I]);
+    });
+  } else {
+    gamma = (R)fp64_node_update<S, MODE, CENTRAL, POLY>(src, dst, g, x, y, z, cp, &guarded);
+  }
   if constexpr (RECORD) {
     gamma_out[nb.ox[1] + nb.oy[1] + nb.oz[1]] = (float)gamma;
     if (guarded) atomicAdd(&ctr->guarded, 1ull);
@@ -811,8 +1232,9 @@ __device__ __forceinline__ void node_update2(const S* src, S* dst, const Geo& g,
     d[I] = Codec2<S>::template load<I, MODE == MODE_PULL>(
         base + na.template at<I, Pat::load_shift>(), base + nb.template at<I, Pat::load_shift>());
   });
-  int guarded;
-  const float2 gamma = collide<float2, CENTRAL, false, POLY>(d, cp, &guarded);
+  int guarded, fp64 = 0;
+  float2 gamma = collide_step<float2, CENTRAL, false, POLY, C::rel>(d, cp, &guarded, &fp64);
+  const bool va = !(fp64 & 1), vbs = vb && !(fp64 & 2);
   // In the AA modes the stores reuse the load addresses' planes; opaque copies of P and dst
   // make the compiler recompute the store addresses instead of keeping 27 64-bit addresses
   // live across the collision (which spilled at 3 blocks per SM).
@@ -839,12 +1261,99 @@ __device__ __forceinline__ void node_update2(const S* src, S* dst, const Geo& g,
     constexpr int I = decltype(ic)::value;
     S* base = dsts + (uint64_t)Pat::store_plane(I) * Ps;
     Codec2<S>::template store<I>(base + sa.template at<I, Pat::store_shift>(),
-                                 base + sb.template at<I, Pat::store_shift>(), vb, d[I]);
+                                 base + sb.template at<I, Pat::store_shift>(), va, vbs, d[I]);
   });
+  if (fp64) {  // lanes whose <dh|dh> fell under kDenFp64: FP64 collision of those nodes
+    int g64 = 0;
+    if (fp64 & 1) {
+      gamma.x = fp64_node_update<S, MODE, CENTRAL, POLY>(src, dst, g, xa, ya, za, cp, &g64);
+      guarded = (guarded & ~1) | g64;
+    }
+    if ((fp64 & 2) && vb) {
+      gamma.y = fp64_node_update<S, MODE, CENTRAL, POLY>(src, dst, g, xb, yb, zb, cp, &g64);
+      guarded = (guarded & ~2) | (g64 << 1);
+    }
+  }
   if constexpr (RECORD) {
     gamma_out[na.ox[1] + na.oy[1] + na.oz[1]] = gamma.x;
     if (vb) gamma_out[nb.ox[1] + nb.oy[1] + nb.oz[1]] = gamma.y;
     const int n = __popc(guarded & (vb ? 3 : 1));
+    if (n) atomicAdd(&ctr->guarded, (unsigned long long)n);
+  }
+}
+
+// Two adjacent nodes (x, x + 1) of one row per thread (x even, nx even), the collision on
+// FP32x2 lanes: the planes the pattern does not shift in x are read and, for the pull and the
+// even AA step, written as one 32/64-bit access per plane; the x-shifted ones as two scalar
+// accesses. The 9 neighbour rows are addressed from 3 + 3 row offsets and 3 x positions,
+// which keeps fewer registers live than two full neighbourhoods. FP32 arithmetic only.
+template <typename S, int MODE, bool RECORD>
+__device__ __forceinline__ void node_update_adj(const S* src, S* dst, const Geo& g, uint32_t x,
+                                                uint32_t y, uint32_t z, const CollideParams& cp,
+                                                float* gamma_out, StepCounters* ctr) {
+  using C = Codec<S>;
+  using Pat = Pattern<MODE>;
+  using IO = PairIO<S>;
+  static_assert(std::is_same<typename C::R, float>::value, "FP32 arithmetic only");
+  uint32_t oy[3], oz[3];
+  oy[0] = (y == 0 ? g.ny - 1 : y - 1) * g.nx;
+  oy[1] = y * g.nx;
+  oy[2] = (y + 1 == g.ny ? 0 : y + 1) * g.nx;
+  oz[0] = (z == 0 ? g.nz - 1 : z - 1) * g.nxy;
+  oz[1] = z * g.nxy;
+  oz[2] = (z + 1 == g.nz ? 0 : z + 1) * g.nxy;
+  const uint32_t xm = x == 0 ? g.nx - 1 : x - 1;
+  const uint32_t xp2 = x + 2 == g.nx ? 0 : x + 2;
+  float2 d[27];
+  Unroll<0, 27>::run([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    constexpr int LS = Pat::load_shift;
+    const S* row = src + (uint64_t)Pat::load_plane(I) * g.P + oy[LS * cy(I) + 1] +
+                   oz[LS * cz(I) + 1];
+    d[I] = IO::template get<LS * cx(I), MODE == MODE_PULL>(row + x, row + xm, row + xp2);
+  });
+  int guarded, fp64 = 0;
+  float2 gamma = collide_step<float2, false, false, false, C::rel>(d, cp, &guarded, &fp64);
+  const bool wa = !(fp64 & 1), wb = !(fp64 & 2);
+  // AA: opaque copies of P and dst keep the compiler from holding 27 addresses across the
+  // collision
+  uint64_t Ps = g.P;
+  S* dsts = dst;
+  if constexpr (MODE != MODE_PULL) asm volatile("" : "+l"(Ps), "+l"(dsts));
+  Unroll<0, 27>::run([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    constexpr int SS = Pat::store_shift;
+    S* row = dsts + (uint64_t)Pat::store_plane(I) * Ps + oy[SS * cy(I) + 1] + oz[SS * cz(I) + 1];
+    constexpr int SX = SS * cx(I);
+    if constexpr (SX == 0) {
+      if (!fp64) {
+        IO::put2(row + x, d[I]);
+      } else {
+        if (wa) IO::put1(row + x, d[I].x);
+        if (wb) IO::put1(row + x + 1, d[I].y);
+      }
+    } else if constexpr (SX > 0) {
+      if (wa) IO::put1(row + x + 1, d[I].x);
+      if (wb) IO::put1(row + xp2, d[I].y);
+    } else {
+      if (wa) IO::put1(row + xm, d[I].x);
+      if (wb) IO::put1(row + x, d[I].y);
+    }
+  });
+  if (fp64) {  // lanes whose <dh|dh> fell under kDenFp64: FP64 collision of those nodes
+    int g64 = 0;
+    if (fp64 & 1) {
+      gamma.x = fp64_node_update<S, MODE, false, false>(src, dst, g, x, y, z, cp, &g64);
+      guarded = (guarded & ~1) | g64;
+    }
+    if (fp64 & 2) {
+      gamma.y = fp64_node_update<S, MODE, false, false>(src, dst, g, x + 1, y, z, cp, &g64);
+      guarded = (guarded & ~2) | (g64 << 1);
+    }
+  }
+  if constexpr (RECORD) {
+    *reinterpret_cast<float2*>(gamma_out + oy[1] + oz[1] + x) = gamma;
+    const int n = __popc(guarded & 3);
     if (n) atomicAdd(&ctr->guarded, (unsigned long long)n);
   }
 }

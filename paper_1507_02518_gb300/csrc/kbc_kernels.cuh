@@ -11,6 +11,7 @@
 #include "kbc_device.cuh"
 #include "kbc_ops.h"
 #include "kbc_staged.cuh"
+#include "kbc_tma.cuh"
 
 namespace kbc {
 
@@ -24,7 +25,7 @@ __global__ void __launch_bounds__(MaxThreads<S>::value) step_kernel(const S* src
                                                    float* gamma_out, StepCounters* ctr) {
   const uint32_t x = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t y = blockIdx.y * blockDim.y + threadIdx.y;
-  const uint32_t z = blockIdx.z;
+  const uint32_t z = blockIdx.z + g.zb;
   if (x >= g.nx || y >= g.ny) return;
   node_update<S, MODE, RECORD, CENTRAL, EXACT, POLY>(src, dst, g, x, y, z, cp, gamma_out, ctr);
 }
@@ -56,9 +57,32 @@ __global__ void __launch_bounds__(128, 3) pair_step_kernel(const S* src, S* dst,
   const uint32_t xa = blockIdx.x * (2 * blockDim.x) + warp * 64 + lane;
   if (xa >= g.nx) return;
   const bool vb = xa + 32 < g.nx;
-  node_update2<S, MODE, RECORD, CENTRAL, POLY>(src, dst, g, xa, blockIdx.y, blockIdx.z,
-                                               vb ? xa + 32 : xa, blockIdx.y, blockIdx.z, vb,
+  const uint32_t z = blockIdx.z + g.zb;
+  node_update2<S, MODE, RECORD, CENTRAL, POLY>(src, dst, g, xa, blockIdx.y, z,
+                                               vb ? xa + 32 : xa, blockIdx.y, z, vb,
                                                cp, gamma_out, ctr);
+}
+
+// Two adjacent nodes per thread, (x, x + 1) with x even: a block of blockDim.x threads covers
+// 2 blockDim.x consecutive nodes of one row (nx even).
+template <typename S, int MODE, bool RECORD>
+__global__ void __launch_bounds__(128, 3) adj_step_kernel(const S* src, S* dst, Geo g,
+                                                       CollideParams cp, float* gamma_out,
+                                                       StepCounters* ctr) {
+  const uint32_t x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (x >= g.nx) return;
+  node_update_adj<S, MODE, RECORD>(src, dst, g, x, blockIdx.y, blockIdx.z + g.zb, cp,
+                                   gamma_out, ctr);
+}
+
+template <typename S, int MODE, bool RECORD>
+static cudaError_t launch_adj(const S* src, S* dst, const Geo& g, const CollideParams& cp,
+                              float* gamma_out, StepCounters* ctr, cudaStream_t st) {
+  const uint32_t pairs = g.nx / 2;
+  const uint32_t threads = pairs >= 128 ? 128 : (pairs + 31) / 32 * 32;
+  const dim3 grid((pairs + threads - 1) / threads, g.ny, g.ze - g.zb);
+  adj_step_kernel<S, MODE, RECORD><<<grid, threads, 0, st>>>(src, dst, g, cp, gamma_out, ctr);
+  return cudaGetLastError();
 }
 
 // The same update over the box's node order instead of rows: block k covers nodes
@@ -70,14 +94,15 @@ __global__ void __launch_bounds__(128, 3) pair_linear_kernel(const S* src, S* ds
                                                           CollideParams cp, float* gamma_out,
                                                           StepCounters* ctr) {
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t n = blockIdx.x * 256 + warp * 64 + lane;  // P < 2^31
-  if (n >= g.P) return;
+  const uint32_t nend = g.ze * g.nxy;  // P < 2^31
+  const uint32_t n = g.zb * g.nxy + blockIdx.x * 256 + warp * 64 + lane;
+  if (n >= nend) return;
   const uint32_t row = n / g.nx;
   const uint32_t xa = n - row * g.nx;
   const uint32_t za = row / g.ny;
   const uint32_t ya = row - za * g.ny;
   uint32_t xb = xa, yb = ya, zb = za;
-  const bool vb = n + 32 < g.P;
+  const bool vb = n + 32 < nend;
   if (vb) advance_node(xb, yb, zb, 32, g.nx, g.ny);
   node_update2<S, MODE, RECORD, CENTRAL, POLY, false>(src, dst, g, xa, ya, za, xb, yb, zb, vb,
                                                       cp, gamma_out, ctr);
@@ -107,12 +132,13 @@ static cudaError_t launch_pair(const S* src, S* dst, const Geo& g, const Collide
                                float* gamma_out, StepCounters* ctr, cudaStream_t st) {
   const uint32_t warps = pair_block_warps(g.nx);
   const uint32_t row_blocks = (g.nx + 64 * warps - 1) / (64 * warps);
+  const uint64_t nodes = (uint64_t)(g.ze - g.zb) * g.nxy;
   if (20 * (uint64_t)g.nx < 19 * (uint64_t)row_blocks * 64 * warps) {
     pair_linear_kernel<S, MODE, RECORD, CENTRAL, POLY>
-        <<<(unsigned)((g.P + 255) / 256), 128, 0, st>>>(src, dst, g, cp, gamma_out, ctr);
+        <<<(unsigned)((nodes + 255) / 256), 128, 0, st>>>(src, dst, g, cp, gamma_out, ctr);
     return cudaGetLastError();
   }
-  const dim3 grid(row_blocks, g.ny, g.nz);
+  const dim3 grid(row_blocks, g.ny, g.ze - g.zb);
   pair_step_kernel<S, MODE, RECORD, CENTRAL, POLY><<<grid, 32 * warps, 0, st>>>(
       src, dst, g, cp, gamma_out, ctr);
   return cudaGetLastError();
@@ -134,6 +160,8 @@ __global__ void __launch_bounds__(MaxThreads<S>::value) batch_kernel(const BoxDe
     g.nz = bd.nz;
     g.nxy = bd.nxy;
     g.P = (uint64_t)bd.nxy * bd.nz;
+    g.zb = 0;
+    g.ze = bd.nz;
     CollideParams cp;
     cp.beta = bd.beta;
     cp.two_beta = bd.two_beta;
@@ -173,6 +201,8 @@ __global__ void __launch_bounds__(128, 3) batch_pair_kernel(const BoxDesc* __res
     g.nz = bd.nz;
     g.nxy = bd.nxy;
     g.P = (uint64_t)bd.nxy * bd.nz;
+    g.zb = 0;
+    g.ze = bd.nz;
     CollideParams cp;
     cp.beta = bd.beta;
     cp.two_beta = bd.two_beta;
@@ -216,6 +246,8 @@ inline Geo make_geo(const BoxView& b) {
   g.nz = b.nz;
   g.nxy = b.nx * b.ny;
   g.P = b.P;
+  g.zb = b.zb;
+  g.ze = b.ze;
   return g;
 }
 
@@ -248,7 +280,7 @@ static cudaError_t launch_step_c(const BoxView& b, const S* src, S* dst, const G
   if constexpr (!POLY) {
     if (cp.gamma_mode == GAMMA_EXACT) {  // one node per thread, whatever kernel was chosen
       const dim3 block(o.bx, o.by, 1);
-      const dim3 grid((b.nx + o.bx - 1) / o.bx, (b.ny + o.by - 1) / o.by, b.nz);
+      const dim3 grid((b.nx + o.bx - 1) / o.bx, (b.ny + o.by - 1) / o.by, g.ze - g.zb);
       step_kernel<S, MODE, RECORD, CENTRAL, true><<<grid, block, 0, st>>>(src, dst, g, cp,
                                                                           b.gamma, ctr);
       return cudaGetLastError();
@@ -262,11 +294,19 @@ static cudaError_t launch_step_c(const BoxView& b, const S* src, S* dst, const G
                                                 (uint32_t)o.prefetch, st);
   }
   if constexpr (!std::is_same<S, double>::value) {
-    if (o.kernel == KERNEL_PACKED || o.kernel == KERNEL_AUTO)
+    if constexpr (!CENTRAL && !POLY) {
+      if (o.kernel == KERNEL_ROWS)
+        return launch_rows<S, MODE, RECORD>(src, dst, g, cp, b.gamma, ctr, o.budget, o.stall, st);
+      // the default for even rows: adjacent pairs (measured faster than (x, x + 32) pairs at
+      // 256^3: FP32 AA 0.549 vs 0.630 ms, FP16 AA 0.446 vs 0.504 ms, pull equal or better)
+      if ((o.kernel == KERNEL_ADJ || o.kernel == KERNEL_AUTO) && g.nx % 2 == 0)
+        return launch_adj<S, MODE, RECORD>(src, dst, g, cp, b.gamma, ctr, st);
+    }
+    if (o.kernel == KERNEL_PACKED || o.kernel == KERNEL_AUTO || o.kernel == KERNEL_ROWS)
       return launch_pair<S, MODE, RECORD, CENTRAL, POLY>(src, dst, g, cp, b.gamma, ctr, st);
   }
   const dim3 block(o.bx, o.by, 1);
-  const dim3 grid((b.nx + o.bx - 1) / o.bx, (b.ny + o.by - 1) / o.by, b.nz);
+  const dim3 grid((b.nx + o.bx - 1) / o.bx, (b.ny + o.by - 1) / o.by, g.ze - g.zb);
   step_kernel<S, MODE, RECORD, CENTRAL, false, POLY><<<grid, block, 0, st>>>(src, dst, g, cp,
                                                                              b.gamma, ctr);
   return cudaGetLastError();
@@ -289,6 +329,24 @@ static cudaError_t launch_step(const BoxView& b, const S* src, S* dst, const Geo
 template <typename S>
 bool Ops<S>::staged_ok(uint32_t nx) {
   return staged_supported<S>(nx);
+}
+
+template <typename S>
+bool Ops<S>::rows_ok(uint32_t nx, uint32_t ny, uint32_t nz) {
+  if constexpr (std::is_same<S, double>::value) {
+    return false;
+  } else {
+    Geo g;
+    g.nx = nx;
+    g.ny = ny;
+    g.nz = nz;
+    g.nxy = nx * ny;
+    g.P = (uint64_t)nx * ny * nz;
+    g.zb = 0;
+    g.ze = nz;
+    RowsArgs a;
+    return rows_shape<S>(g, &a);
+  }
 }
 
 template <typename S>

@@ -16,6 +16,7 @@ struct BoxView {
   int central;         // shear part in the central-moment basis
   int poly;            // polynomial equilibrium eq:polynomial2 instead of the product form
   int scheme;          // 0 pull, 1 AA
+  uint32_t zb, ze;     // planes zb <= z < ze are stepped (a whole box: 0, nz)
 };
 
 // counters written by the step kernels: guard events of the recorded collision, and a flag
@@ -32,7 +33,9 @@ enum {
   KERNEL_DIRECT = 1,
   KERNEL_STAGED = 2,
   KERNEL_PERSISTENT = 3,
-  KERNEL_PACKED = 4
+  KERNEL_PACKED = 4,
+  KERNEL_ROWS = 5,
+  KERNEL_ADJ = 6
 };
 struct StepOpts {
   int bx, by;                 // block of the direct kernel
@@ -66,6 +69,8 @@ template <typename S> struct Ops {
                           StepCounters* counters, cudaStream_t st);
   // whether the staged (bulk-copy pipelined) kernel supports this row length
   static bool staged_ok(uint32_t nx);
+  // whether the row-staged pair kernel (KERNEL_ROWS) takes this box
+  static bool rows_ok(uint32_t nx, uint32_t ny, uint32_t nz);
   // canonical f(t) = f_eq(rho, u) for nodes [n0, n0 + cnt) (rho may be null: 1)
   static cudaError_t init(const BoxView& b, int64_t t, const double* rho, const double* u,
                           uint64_t n0, uint64_t cnt, uint64_t ld, cudaStream_t st);

@@ -86,7 +86,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 
 struct StagedArgs {
   uint32_t nseg;     // x-segments per row
-  uint32_t nitems;   // nseg * ny * nz
+  uint32_t nitems;   // nseg * ny * (ze - zb)
   unsigned long long budget;  // wait budget in SM cycles
   int stall;         // test hook: issue no copies, so every wait runs out
 };
@@ -100,7 +100,7 @@ __device__ __forceinline__ void staged_issue(const S* src, const Geo& g, const S
   constexpr int H = L::H;
   const int lane = threadIdx.x & 31;
   const uint32_t seg = item % a.nseg;
-  const uint32_t row = item / a.nseg;
+  const uint32_t row = item / a.nseg + g.zb * g.ny;
   const uint32_t y = row % g.ny, z = row / g.ny;
   const uint32_t x0 = seg * kSeg;
   const uint32_t cnt = min((uint32_t)kSeg, g.nx - x0);
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kSeg, StagedCfg<S>::min_blocks) staged_step_ke
       return;
     }
     const uint32_t seg = item % a.nseg;
-    const uint32_t row = item / a.nseg;
+    const uint32_t row = item / a.nseg + g.zb * g.ny;
     const uint32_t y = row % g.ny, z = row / g.ny;
     const uint32_t x0 = seg * kSeg;
     const uint32_t cnt = min((uint32_t)kSeg, g.nx - x0);
@@ -179,17 +179,23 @@ __global__ void __launch_bounds__(kSeg, StagedCfg<S>::min_blocks) staged_step_ke
       R d[27];
       Unroll<0, 27>::run([&](auto ic) {
         constexpr int I = decltype(ic)::value;
-        d[I] = C::template load<I>(sb + I * L::ROW + H + tid + Pat::load_shift * cx(I));
+        d[I] = C::template load_raw<I>(sb + I * L::ROW + H + tid + Pat::load_shift * cx(I));
       });
-      int guarded;
-      const R gamma = collide<R>(d, cp, &guarded);
+      int guarded, fp64 = 0;
+      const uint32_t x = x0 + tid;
+      R gamma = collide_step<R, false, false, false, C::rel>(
+          d, cp, &guarded, std::is_same<R, float>::value ? &fp64 : nullptr);
       Nbr nb;
-      nb.init(g, x0 + tid, y, z);
-      Unroll<0, 27>::run([&](auto ic) {
-        constexpr int I = decltype(ic)::value;
-        S* p = dst + (uint64_t)Pat::store_plane(I) * g.P + nb.template at<I, Pat::store_shift>();
-        C::template store<I>(p, d[I]);
-      });
+      nb.init(g, x, y, z);
+      if (!fp64) {
+        Unroll<0, 27>::run([&](auto ic) {
+          constexpr int I = decltype(ic)::value;
+          S* p = dst + (uint64_t)Pat::store_plane(I) * g.P + nb.template at<I, Pat::store_shift>();
+          C::template store_raw<I>(p, d[I]);
+        });
+      } else {  // <dh|dh> under kDenFp64: FP64 collision of this node from global memory
+        gamma = (R)fp64_node_update<S, MODE, false, false>(src, dst, g, x, y, z, cp, &guarded);
+      }
       if constexpr (RECORD) {
         gamma_out[nb.ox[1] + nb.oy[1] + nb.oz[1]] = (float)gamma;
         if (guarded) atomicAdd(&ctr->guarded, 1ull);
@@ -228,7 +234,7 @@ __device__ __forceinline__ void prefetch_item(const S* src, const Geo& g, const 
                                               uint32_t item, int lane) {
   using Pat = Pattern<MODE>;
   const uint32_t seg = item % a.nseg;
-  const uint32_t row = item / a.nseg;
+  const uint32_t row = item / a.nseg + g.zb * g.ny;
   const uint32_t y = row % g.ny, z = row / g.ny;
   const uint32_t x0 = seg * kSeg;
   const uint32_t cnt = min((uint32_t)kSeg, g.nx - x0);
@@ -256,7 +262,7 @@ __global__ void __launch_bounds__(kSeg, PersistCfg<S>::min_blocks)
       if (ahead < a.nitems) prefetch_item<S, MODE>(src, g, a, ahead, tid);
     }
     const uint32_t seg = item % a.nseg;
-    const uint32_t row = item / a.nseg;
+    const uint32_t row = item / a.nseg + g.zb * g.ny;
     const uint32_t y = row % g.ny, z = row / g.ny;
     const uint32_t x = seg * kSeg + tid;
     if (x < g.nx) node_update<S, MODE, RECORD>(src, dst, g, x, y, z, cp, gamma_out, ctr);
@@ -280,7 +286,7 @@ cudaError_t launch_persistent(const S* src, S* dst, const Geo& g, const CollideP
   }
   PersistArgs a;
   a.nseg = (g.nx + kSeg - 1) / kSeg;
-  a.nitems = a.nseg * g.ny * g.nz;
+  a.nitems = a.nseg * g.ny * (g.ze - g.zb);
   a.prefetch = (((uint64_t)g.nx * sizeof(S)) % 16 == 0) ? prefetch : 0;
   const uint32_t cap = (uint32_t)(sms * blocks_per_sm);
   const uint32_t grid = a.nitems < cap ? a.nitems : cap;
@@ -314,7 +320,7 @@ cudaError_t launch_staged(const S* src, S* dst, const Geo& g, const CollideParam
   }
   StagedArgs a;
   a.nseg = (g.nx + kSeg - 1) / kSeg;
-  a.nitems = a.nseg * g.ny * g.nz;
+  a.nitems = a.nseg * g.ny * (g.ze - g.zb);
   a.budget = budget;
   a.stall = stall;
   const uint32_t cap = (uint32_t)(sms * blocks_per_sm);

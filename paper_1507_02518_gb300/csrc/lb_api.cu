@@ -176,6 +176,67 @@ const void* mapped_host(const void* p) {
   return (a.type == cudaMemoryTypeHost) ? a.devicePointer : nullptr;
 }
 
+
+// ---------------------------------------------------------------- slab faces
+// A face is 9 population planes (plane0 .. plane0 + 8: the velocities with v_z = -1 or +1) of
+// one z-plane of a slab's local box; each is a contiguous run of nx ny values, the runs P
+// values apart. face_kernel copies two faces between the population array and two contiguous
+// buffers [9][nx ny] (to_buffer: pack; otherwise unpack), in units of U (16 bytes when every
+// run is a multiple of 16 bytes, else 2 bytes).
+struct FaceSpec {
+  uint32_t plane0, z;
+};
+
+template <typename U>
+__global__ void face_kernel(char* pops, uint64_t plane_bytes, uint64_t zplane_bytes,
+                            FaceSpec f0, FaceSpec f1, char* buf0, char* buf1, int to_buffer) {
+  const uint64_t run = zplane_bytes / sizeof(U);  // units per population plane of a face
+  const uint64_t per_face = 9 * run;
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < 2 * per_face;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    const int which = k >= per_face;
+    const uint64_t q = which ? k - per_face : k;
+    const FaceSpec f = which ? f1 : f0;
+    const uint64_t j = q / run, e = q - j * run;
+    U* p = reinterpret_cast<U*>(pops + (f.plane0 + j) * plane_bytes + f.z * zplane_bytes) + e;
+    U* b = reinterpret_cast<U*>(which ? buf1 : buf0) + q;
+    if (to_buffer)
+      *b = *p;
+    else
+      *p = *b;
+  }
+}
+
+// Which faces a slab sends and receives after a step (local planes: 0 and nz + 1 are the halo
+// planes, 1 .. nz the slab's own). Pull: the outgoing populations of the boundary planes of
+// the buffer just written go to the neighbours' halos. AA, even step: the boundary planes'
+// slots that the neighbours' odd step reads. AA, odd step: the halo slots this slab's odd step
+// wrote, which belong to the neighbours' boundary planes.
+struct SlabFaces {
+  FaceSpec send_up, send_down, recv_below, recv_above;
+};
+SlabFaces slab_faces(int scase, uint32_t nz) {
+  const uint32_t m = 0, p = 18;  // first plane of v_z = -1, of v_z = +1
+  SlabFaces f;
+  if (scase == 0) {           // pull
+    f.send_up = {p, nz};
+    f.send_down = {m, 1};
+    f.recv_below = {p, 0};
+    f.recv_above = {m, nz + 1};
+  } else if (scase == 1) {    // AA, after an even step
+    f.send_up = {m, nz};
+    f.send_down = {p, 1};
+    f.recv_below = {m, 0};
+    f.recv_above = {p, nz + 1};
+  } else {                    // AA, after an odd step
+    f.send_up = {p, nz + 1};
+    f.send_down = {m, 0};
+    f.recv_below = {p, 1};
+    f.recv_above = {m, nz};
+  }
+  return f;
+}
+
 }  // namespace
 
 void kbc_set_thread_error(const std::string& msg) { g_create_error = msg; }
@@ -202,6 +263,20 @@ struct lb_ctx {
   // set when a step kernel's bounded wait ran out: the populations are not a valid state
   // until lb_set_populations, lb_init_field or lb_presolve rewrites them
   bool needs_reset = false;
+  // nodes the transfer calls expose, in the context's node numbering: the whole box, or a
+  // slab's own planes (between its halo planes)
+  uint64_t n_first = 0, n_count = 0;
+  // slab of a box split along z (lb_slab_create): its first global plane and plane count, the
+  // face buffers (send up, send down, receive from below, receive from above), the exchange
+  // pattern of the step whose faces were packed, and where the step stands (0 stepped and
+  // unpacked, 1 faces stepped and packed, 2 stepped, faces not yet unpacked)
+  bool slab = false;
+  int32_t slab_z0 = 0, slab_nz = 0, slab_nz_total = 0;
+  void* face[4] = {nullptr, nullptr, nullptr, nullptr};
+  size_t face_bytes = 0;
+  int slab_case = 0;
+  int slab_phase = 0;
+  bool slab_record = false;
   std::string err;
 };
 
@@ -241,6 +316,10 @@ void setup_ctx(lb_ctx* c, const lb_config* cfg, char* base, const BoxLayout& B,
   c->box.poly = cfg->equilibrium == LB_EQ_POLY2;
   c->box.gamma_mode = cfg->gamma_mode;
   c->box.scheme = cfg->scheme;
+  c->box.zb = 0;
+  c->box.ze = (uint32_t)cfg->nz;
+  c->n_first = 0;
+  c->n_count = c->box.P;
   c->counters = (kbc::StepCounters*)(base + B.counters);
   c->stream = st;
   c->ufield = base + S.ufield;
@@ -294,10 +373,38 @@ lb_status sync(lb_ctx* c, const char* what) {
 
 // Calls that read or advance the state refuse to run on a state left invalid by a timeout.
 lb_status check_state(lb_ctx* c, const char* what) {
+  if (c->slab && c->slab_phase != 0)
+    return fail(c, LB_ERR_INVALID_ARG, std::string(what) + ": the slab's step is not complete "
+                                       "(lb_slab_step_interior, then lb_slab_unpack)");
   if (!c->needs_reset) return LB_OK;
   return fail(c, LB_ERR_TIMEOUT, std::string(what) + ": the state is not valid after a timed-"
                                  "out step; call lb_set_populations, lb_init_field or "
                                  "lb_presolve first");
+}
+
+cudaError_t launch_faces(lb_ctx* c, char* pops, FaceSpec f0, FaceSpec f1, void* b0, void* b1,
+                         int to_buffer) {
+  const uint64_t es = elem_size(c->cfg.storage);
+  const uint64_t zplane = (uint64_t)c->box.nx * c->box.ny * es;
+  const uint64_t plane = c->box.P * es;
+  const uint64_t units16 = 2 * 9 * (zplane / 16);
+  if (zplane % 16 == 0) {
+    const int grid = (int)std::min<uint64_t>((units16 + 255) / 256, 152ull * 8);
+    face_kernel<uint4><<<grid, 256, 0, c->stream>>>(pops, plane, zplane, f0, f1, (char*)b0,
+                                                    (char*)b1, to_buffer);
+  } else {
+    const uint64_t units2 = 2 * 9 * (zplane / 2);
+    const int grid = (int)std::min<uint64_t>((units2 + 255) / 256, 152ull * 8);
+    face_kernel<uint16_t><<<grid, 256, 0, c->stream>>>(pops, plane, zplane, f0, f1, (char*)b0,
+                                                       (char*)b1, to_buffer);
+  }
+  return cudaGetLastError();
+}
+
+lb_status slab_only(lb_ctx* c, const char* what) {
+  if (!c) return LB_ERR_INVALID_ARG;
+  if (!c->slab) return fail(c, LB_ERR_INVALID_ARG, std::string(what) + " needs a slab context");
+  return LB_OK;
 }
 
 kbc::StepOpts step_opts(const lb_ctx* c) {
@@ -389,19 +496,20 @@ lb_status lb_init_field(lb_ctx* c, const double* rho, const double* u, int on_de
   if (!c) return LB_ERR_INVALID_ARG;
   if (!u) return fail(c, LB_ERR_INVALID_ARG, "u is NULL");
   c->needs_reset = false;  // the state is rewritten
-  const uint64_t P = c->box.P;
+  c->slab_phase = 0;
+  const uint64_t P = c->n_count, nb = c->n_first;  // nodes exposed through the API
   c->t = 0;
   c->gamma_valid = false;
   cudaError_t e;
   if (on_device) {
-    e = dispatch(c, [&](auto ops) { return ops.init(c->box, 0, rho, u, 0, P, P, c->stream); });
+    e = dispatch(c, [&](auto ops) { return ops.init(c->box, 0, rho, u, nb, P, P, c->stream); });
     if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
     return LB_OK;
   }
   const double* mu = (const double*)mapped_host(u);
   const double* mrho = (const double*)mapped_host(rho);
   if (mu && (!rho || mrho)) {  // page-locked inputs: the kernel reads them in place
-    e = dispatch(c, [&](auto ops) { return ops.init(c->box, 0, mrho, mu, 0, P, P, c->stream); });
+    e = dispatch(c, [&](auto ops) { return ops.init(c->box, 0, mrho, mu, nb, P, P, c->stream); });
     if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
     return sync(c, "init");
   }
@@ -415,7 +523,7 @@ lb_status lb_init_field(lb_ctx* c, const double* rho, const double* u, int on_de
       e = cudaMemcpyAsync(su + a * cnt, u + a * P + n0, cnt * 8, cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "copying initial fields");
     e = dispatch(c, [&](auto ops) {
-      return ops.init(c->box, 0, rho ? srho : nullptr, su, n0, cnt, cnt, c->stream);
+      return ops.init(c->box, 0, rho ? srho : nullptr, su, nb + n0, cnt, cnt, c->stream);
     });
     if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
   }
@@ -430,6 +538,7 @@ lb_status lb_presolve(lb_ctx* c, const double* u0, int on_device, double nu_pre,
   if (!u0) return fail(c, LB_ERR_INVALID_ARG, "u0 is NULL");
   if (!(nu_pre > 0.0) || !std::isfinite(nu_pre))
     return fail(c, LB_ERR_INVALID_ARG, "nu_pre must be finite and > 0");
+  if (c->slab) return fail(c, LB_ERR_UNSUPPORTED, "the pre-solve runs on whole boxes");
   if (max_iters < 0) return fail(c, LB_ERR_INVALID_ARG, "max_iters must be >= 0");
   if (std::isnan(tol)) return fail(c, LB_ERR_INVALID_ARG, "tol is NaN");
   if (from_current && c->t != 0)
@@ -438,6 +547,7 @@ lb_status lb_presolve(lb_ctx* c, const double* u0, int on_device, double nu_pre,
     if (lb_status cs = check_state(c, "presolve"); cs != LB_OK) return cs;
   }
   c->needs_reset = false;  // the state is rewritten
+  c->slab_phase = 0;
   const uint64_t P = c->box.P;
   const double beta_pre = 1.0 / (6.0 * nu_pre + 1.0);
   c->t = 0;
@@ -529,6 +639,9 @@ lb_status lb_step(lb_ctx* c, int64_t n) {
   Range range_("lb_step");
   if (!c) return LB_ERR_INVALID_ARG;
   if (n < 0) return fail(c, LB_ERR_INVALID_ARG, "n must be >= 0");
+  if (c->slab)
+    return fail(c, LB_ERR_INVALID_ARG, "a slab context steps with lb_slab_step_faces, "
+                                       "lb_slab_step_interior and lb_slab_unpack");
   if (lb_status cs = check_state(c, "step"); cs != LB_OK) return cs;
   for (int64_t k = 0; k < n; ++k) {
     const bool record = (k == n - 1);
@@ -550,7 +663,7 @@ lb_status lb_moments(lb_ctx* c, double* rho, double* u, int on_device) {
   if (!c) return LB_ERR_INVALID_ARG;
   if (!u) return fail(c, LB_ERR_INVALID_ARG, "u is NULL");
   if (lb_status cs = check_state(c, "moments"); cs != LB_OK) return cs;
-  const uint64_t P = c->box.P;
+  const uint64_t P = c->n_count, nb = c->n_first;  // nodes exposed through the API
   cudaError_t e;
   if (!on_device) {  // page-locked outputs: the kernel writes them in place
     double* mu = (double*)mapped_host(u);
@@ -562,7 +675,7 @@ lb_status lb_moments(lb_ctx* c, double* rho, double* u, int on_device) {
     }
   }
   if (on_device) {
-    e = dispatch(c, [&](auto ops) { return ops.moments(c->box, c->t, rho, u, 0, P, P, c->stream); });
+    e = dispatch(c, [&](auto ops) { return ops.moments(c->box, c->t, rho, u, nb, P, P, c->stream); });
     if (e != cudaSuccess) return cuda_fail(c, e, "moments kernel");
     return sync(c, "moments");
   }
@@ -571,7 +684,7 @@ lb_status lb_moments(lb_ctx* c, double* rho, double* u, int on_device) {
     double* srho = c->staging;
     double* su = c->staging + cnt;
     e = dispatch(c, [&](auto ops) {
-      return ops.moments(c->box, c->t, srho, su, n0, cnt, cnt, c->stream);
+      return ops.moments(c->box, c->t, srho, su, nb + n0, cnt, cnt, c->stream);
     });
     if (e != cudaSuccess) return cuda_fail(c, e, "moments kernel");
     if (rho) e = cudaMemcpyAsync(rho + n0, srho, cnt * 8, cudaMemcpyDeviceToHost, c->stream);
@@ -585,6 +698,9 @@ lb_status lb_moments(lb_ctx* c, double* rho, double* u, int on_device) {
 lb_status lb_diagnostics(lb_ctx* c, lb_diag* out) {
   Range range_("lb_diagnostics");
   if (!c || !out) return c ? fail(c, LB_ERR_INVALID_ARG, "out is NULL") : LB_ERR_INVALID_ARG;
+  if (c->slab)
+    return fail(c, LB_ERR_UNSUPPORTED, "diagnostics of a slab need its neighbours' velocities; "
+                                       "gather the slabs' moments instead");
   if (lb_status cs = check_state(c, "diagnostics"); cs != LB_OK) return cs;
   cudaError_t e = dispatch(c, [&](auto ops) {
     return ops.diag(c->box, c->t, c->gamma_valid, c->diag_order, c->ufield, c->partials,
@@ -660,6 +776,7 @@ lb_status lb_spectrum(lb_ctx* c, void* work, size_t work_bytes, int32_t nbins, d
   Range range_("lb_spectrum");
   if (!c) return LB_ERR_INVALID_ARG;
   if (!work || !E) return fail(c, LB_ERR_INVALID_ARG, "work or E is NULL");
+  if (c->slab) return fail(c, LB_ERR_UNSUPPORTED, "the spectrum needs the whole box");
   if (lb_status cs = check_state(c, "spectrum"); cs != LB_OK) return cs;
   lb_status st;
   if (!spectrum_args(c, nbins, &st)) return st;
@@ -689,6 +806,7 @@ lb_status lb_set_diag_order(lb_ctx* c, int32_t order) {
 lb_status lb_stabilizer_gap(lb_ctx* c, lb_gap* out) {
   Range range_("lb_stabilizer_gap");
   if (!c || !out) return c ? fail(c, LB_ERR_INVALID_ARG, "out is NULL") : LB_ERR_INVALID_ARG;
+  if (c->slab) return fail(c, LB_ERR_UNSUPPORTED, "the stabilizer gap runs on whole boxes");
   if (lb_status cs = check_state(c, "stabilizer gap"); cs != LB_OK) return cs;
   if (c->box.poly)
     return fail(c, LB_ERR_UNSUPPORTED, "the stabilizer gap is built for the product-form "
@@ -719,20 +837,20 @@ lb_status lb_get_populations(lb_ctx* c, double* f, int on_device) {
   if (!c) return LB_ERR_INVALID_ARG;
   if (!f) return fail(c, LB_ERR_INVALID_ARG, "f is NULL");
   if (lb_status cs = check_state(c, "get_populations"); cs != LB_OK) return cs;
-  const uint64_t P = c->box.P;
+  const uint64_t P = c->n_count, nb = c->n_first;  // nodes exposed through the API
   cudaError_t e;
   if (!on_device && mapped_host(f)) {  // page-locked output: written in place
     f = (double*)mapped_host(f);
     on_device = 1;
   }
   if (on_device) {
-    e = dispatch(c, [&](auto ops) { return ops.get(c->box, c->t, f, 0, P, P, c->stream); });
+    e = dispatch(c, [&](auto ops) { return ops.get(c->box, c->t, f, nb, P, P, c->stream); });
     if (e != cudaSuccess) return cuda_fail(c, e, "export kernel");
     return sync(c, "get_populations");
   }
   for (uint64_t n0 = 0; n0 < P; n0 += c->stage_nodes) {
     const uint64_t cnt = (P - n0 < c->stage_nodes) ? P - n0 : c->stage_nodes;
-    e = dispatch(c, [&](auto ops) { return ops.get(c->box, c->t, c->staging, n0, cnt, cnt, c->stream); });
+    e = dispatch(c, [&](auto ops) { return ops.get(c->box, c->t, c->staging, nb + n0, cnt, cnt, c->stream); });
     if (e != cudaSuccess) return cuda_fail(c, e, "export kernel");
     for (int i = 0; i < 27 && e == cudaSuccess; ++i)
       e = cudaMemcpyAsync(f + i * P + n0, c->staging + i * cnt, cnt * 8, cudaMemcpyDeviceToHost,
@@ -742,12 +860,27 @@ lb_status lb_get_populations(lb_ctx* c, double* f, int on_device) {
   return sync(c, "get_populations");
 }
 
+lb_status lb_get_gamma(lb_ctx* c, float* gamma, int on_device) {
+  Range range_("lb_get_gamma");
+  if (!c) return LB_ERR_INVALID_ARG;
+  if (!gamma) return fail(c, LB_ERR_INVALID_ARG, "gamma is NULL");
+  if (lb_status cs = check_state(c, "get_gamma"); cs != LB_OK) return cs;
+  if (!c->gamma_valid)
+    return fail(c, LB_ERR_INVALID_ARG, "no collision has been recorded since the state was set");
+  cudaError_t e = cudaMemcpyAsync(gamma, c->box.gamma + c->n_first, c->n_count * sizeof(float),
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "copying the gamma field");
+  return sync(c, "get_gamma");
+}
+
 lb_status lb_set_populations(lb_ctx* c, const double* f, int on_device) {
   Range range_("lb_set_populations");
   if (!c) return LB_ERR_INVALID_ARG;
   if (!f) return fail(c, LB_ERR_INVALID_ARG, "f is NULL");
   c->needs_reset = false;  // the state is rewritten
-  const uint64_t P = c->box.P;
+  c->slab_phase = 0;
+  const uint64_t P = c->n_count, nb = c->n_first;  // nodes exposed through the API
   c->gamma_valid = false;
   cudaError_t e;
   if (!on_device && mapped_host(f)) {  // page-locked input: read in place
@@ -755,7 +888,7 @@ lb_status lb_set_populations(lb_ctx* c, const double* f, int on_device) {
     on_device = 1;
   }
   if (on_device) {
-    e = dispatch(c, [&](auto ops) { return ops.set(c->box, c->t, f, 0, P, P, c->stream); });
+    e = dispatch(c, [&](auto ops) { return ops.set(c->box, c->t, f, nb, P, P, c->stream); });
     if (e != cudaSuccess) return cuda_fail(c, e, "import kernel");
     return sync(c, "set_populations");
   }
@@ -766,7 +899,7 @@ lb_status lb_set_populations(lb_ctx* c, const double* f, int on_device) {
       e = cudaMemcpyAsync(c->staging + i * cnt, f + i * P + n0, cnt * 8, cudaMemcpyHostToDevice,
                           c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "copying populations");
-    e = dispatch(c, [&](auto ops) { return ops.set(c->box, c->t, c->staging, n0, cnt, cnt, c->stream); });
+    e = dispatch(c, [&](auto ops) { return ops.set(c->box, c->t, c->staging, nb + n0, cnt, cnt, c->stream); });
     if (e != cudaSuccess) return cuda_fail(c, e, "import kernel");
   }
   return sync(c, "set_populations");
@@ -785,9 +918,37 @@ lb_status lb_set_time(lb_ctx* c, int64_t t) {
 
 lb_status lb_set_kernel(lb_ctx* c, int32_t kind) {
   if (!c) return LB_ERR_INVALID_ARG;
-  if (kind < LB_KERNEL_AUTO || kind > LB_KERNEL_PACKED)
+  if (kind < LB_KERNEL_AUTO || kind > LB_KERNEL_ADJ)
     return fail(c, LB_ERR_INVALID_ARG, "kind must be LB_KERNEL_AUTO, _DIRECT, _STAGED, "
-                                       "_PERSISTENT or _PACKED");
+                                       "_PERSISTENT, _PACKED, _ROWS or _ADJ");
+  if (kind == LB_KERNEL_ADJ) {
+    if (c->cfg.storage == LB_F64)
+      return fail(c, LB_ERR_UNSUPPORTED, "the adjacent-pair kernel needs FP32 arithmetic "
+                                         "(LB_F32 or LB_F16 storage)");
+    if (c->box.poly || c->box.central)
+      return fail(c, LB_ERR_UNSUPPORTED, "the adjacent-pair kernel implements the product-form "
+                                         "equilibrium and the natural-moment variants only");
+    if (c->box.nx % 2 != 0)
+      return fail(c, LB_ERR_UNSUPPORTED, "the adjacent-pair kernel needs an even nx");
+  }
+  if (kind == LB_KERNEL_ROWS) {
+    if (c->cfg.storage == LB_F64)
+      return fail(c, LB_ERR_UNSUPPORTED, "the rows kernel needs FP32 arithmetic (LB_F32 or "
+                                         "LB_F16 storage)");
+    if (c->box.poly || c->box.central)
+      return fail(c, LB_ERR_UNSUPPORTED, "the rows kernel implements the product-form "
+                                         "equilibrium and the natural-moment variants only");
+    bool ok = false;
+    dispatch(c, [&](auto ops) {
+      ok = ops.rows_ok(c->box.nx, c->box.ny, c->box.nz);
+      return cudaSuccess;
+    });
+    if (!ok)
+      return fail(c, LB_ERR_UNSUPPORTED, "the rows kernel does not take this box shape (nx even, "
+                                         "nx * sizeof(value) % 16 == 0, nx <= 256 with a tile of "
+                                         "R rows, R | ny, R * nx a multiple of 64 in [128, 256], "
+                                         "or nx a multiple of 256)");
+  }
   if ((kind == LB_KERNEL_STAGED || kind == LB_KERNEL_PERSISTENT) && c->box.poly)
     return fail(c, LB_ERR_UNSUPPORTED, "the staged and persistent kernels implement the "
                                        "product-form equilibrium only");
@@ -840,6 +1001,175 @@ lb_status lb_set_block(lb_ctx* c, int32_t bx, int32_t by) {
     return fail(c, LB_ERR_INVALID_ARG, "FP64 storage allows at most 256 threads per block");
   c->bx = bx;
   c->by = by;
+  return LB_OK;
+}
+
+
+// ---------------------------------------------------------------- slabs of a box split along z
+
+size_t lb_slab_required_bytes(const lb_config* global, int32_t nz_local) {
+  std::string why;
+  if (!valid_config(global, &why) || nz_local < 1 || nz_local > global->nz) return 0;
+  lb_config lc = *global;
+  lc.nz = nz_local + 2;
+  if (!valid_config(&lc, &why)) return 0;
+  const BoxLayout B = box_layout(&lc, 0);
+  const SharedLayout S = shared_layout(lc.storage, (uint64_t)lc.nx * lc.ny * lc.nz, B.total);
+  const size_t fb = align_up((size_t)9 * lc.nx * lc.ny * elem_size(lc.storage));
+  return S.total + 4 * fb;
+}
+
+lb_status lb_slab_create(const lb_config* global, int32_t z0, int32_t nz_local, void* dev_buf,
+                         size_t bytes, void* stream, lb_ctx** out) {
+  return no_throw([&]() -> lb_status {
+    if (!out) {
+      g_create_error = "out is NULL";
+      return LB_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    std::string why;
+    if (!valid_config(global, &why)) {
+      g_create_error = why;
+      return LB_ERR_INVALID_ARG;
+    }
+    if (nz_local < 1 || z0 < 0 || z0 >= global->nz || nz_local > global->nz - z0) {
+      g_create_error = "need 0 <= z0 and 1 <= nz_local with z0 + nz_local <= nz";
+      return LB_ERR_INVALID_ARG;
+    }
+    if (global->equilibrium == LB_EQ_POLY2 && global->gamma_mode == LB_GAMMA_EXACT) {
+      g_create_error = "the exact stabilizer is built for the product-form equilibrium only";
+      return LB_ERR_UNSUPPORTED;
+    }
+    lb_config lc = *global;
+    lc.nz = nz_local + 2;
+    if (!valid_config(&lc, &why)) {
+      g_create_error = "slab: " + why;
+      return LB_ERR_INVALID_ARG;
+    }
+    if (!dev_buf || ((uintptr_t)dev_buf % kAlign) != 0) {
+      g_create_error = "dev_buf must be a non-NULL 256-byte aligned device pointer";
+      return LB_ERR_INVALID_ARG;
+    }
+    const size_t need = lb_slab_required_bytes(global, nz_local);
+    if (bytes < need) {
+      char buf[160];
+      snprintf(buf, sizeof buf, "buffer of %zu bytes is smaller than the %zu bytes required",
+               bytes, need);
+      g_create_error = buf;
+      return LB_ERR_OOM;
+    }
+    lb_status s = check_device(&why);
+    if (s != LB_OK) {
+      g_create_error = why;
+      return s;
+    }
+    lb_ctx* c = new lb_ctx();
+    char* base = (char*)dev_buf;
+    const BoxLayout B = box_layout(&lc, 0);
+    const SharedLayout S = shared_layout(lc.storage, (uint64_t)lc.nx * lc.ny * lc.nz, B.total);
+    setup_ctx(c, &lc, base, B, S, (cudaStream_t)stream);
+    c->slab = true;
+    c->slab_z0 = z0;
+    c->slab_nz = nz_local;
+    c->slab_nz_total = global->nz;
+    const uint64_t nxy = (uint64_t)lc.nx * lc.ny;
+    c->n_first = nxy;
+    c->n_count = nxy * (uint64_t)nz_local;
+    c->box.zb = 1;
+    c->box.ze = (uint32_t)nz_local + 1;
+    c->face_bytes = (size_t)9 * nxy * elem_size(lc.storage);
+    const size_t fb = align_up(c->face_bytes);
+    for (int k = 0; k < 4; ++k) c->face[k] = base + S.total + k * fb;
+    s = zero_state(c);
+    if (s != LB_OK) {
+      g_create_error = c->err;
+      delete c;
+      return s;
+    }
+    *out = c;
+    return LB_OK;
+  });
+}
+
+lb_status lb_slab_faces(lb_ctx* c, void** send_up, void** send_down, void** recv_below,
+                        void** recv_above, size_t* face_bytes) {
+  if (lb_status s = slab_only(c, "lb_slab_faces"); s != LB_OK) return s;
+  if (send_up) *send_up = c->face[0];
+  if (send_down) *send_down = c->face[1];
+  if (recv_below) *recv_below = c->face[2];
+  if (recv_above) *recv_above = c->face[3];
+  if (face_bytes) *face_bytes = c->face_bytes;
+  return LB_OK;
+}
+
+lb_status lb_slab_step_faces(lb_ctx* c, int32_t record) {
+  Range range_("lb_slab_step_faces");
+  if (lb_status s = slab_only(c, "lb_slab_step_faces"); s != LB_OK) return s;
+  if (lb_status cs = check_state(c, "slab step"); cs != LB_OK) return cs;
+  if (c->slab_phase != 0)
+    return fail(c, LB_ERR_INVALID_ARG, "the previous step's faces are not unpacked yet "
+                                       "(lb_slab_step_interior, then lb_slab_unpack)");
+  cudaError_t e = cudaSuccess;
+  if (record)
+    e = cudaMemsetAsync(&c->counters->guarded, 0, sizeof(unsigned long long), c->stream);
+  const uint32_t nz = (uint32_t)c->slab_nz;
+  // the boundary planes (local 1 and nz) first, so that their faces can travel while the
+  // interior planes are stepped
+  for (int k = 0; k < (nz > 1 ? 2 : 1) && e == cudaSuccess; ++k) {
+    const uint32_t z = k == 0 ? 1 : nz;
+    c->box.zb = z;
+    c->box.ze = z + 1;
+    e = dispatch(c, [&](auto ops) {
+      return ops.step(c->box, c->t, record != 0, step_opts(c), c->counters, c->stream);
+    });
+  }
+  c->box.zb = 1;
+  c->box.ze = nz + 1;
+  if (e != cudaSuccess) return cuda_fail(c, e, "slab boundary step");
+  const int scase = c->cfg.scheme == LB_PULL ? 0 : ((c->t & 1) == 0 ? 1 : 2);
+  char* pops = (char*)c->box.pop[c->cfg.scheme == LB_PULL ? ((c->t + 1) & 1) : 0];
+  const SlabFaces f = slab_faces(scase, nz);
+  e = launch_faces(c, pops, f.send_up, f.send_down, c->face[0], c->face[1], 1);
+  if (e != cudaSuccess) return cuda_fail(c, e, "packing slab faces");
+  c->slab_case = scase;
+  c->slab_phase = 1;
+  c->slab_record = record != 0;
+  return LB_OK;
+}
+
+lb_status lb_slab_step_interior(lb_ctx* c) {
+  Range range_("lb_slab_step_interior");
+  if (lb_status s = slab_only(c, "lb_slab_step_interior"); s != LB_OK) return s;
+  if (c->slab_phase != 1)
+    return fail(c, LB_ERR_INVALID_ARG, "call lb_slab_step_faces first");
+  const uint32_t nz = (uint32_t)c->slab_nz;
+  cudaError_t e = cudaSuccess;
+  if (nz > 2) {
+    c->box.zb = 2;
+    c->box.ze = nz;
+    e = dispatch(c, [&](auto ops) {
+      return ops.step(c->box, c->t, c->slab_record, step_opts(c), c->counters, c->stream);
+    });
+    c->box.zb = 1;
+    c->box.ze = nz + 1;
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "slab interior step");
+  c->t += 1;
+  c->gamma_valid = c->slab_record;
+  c->slab_phase = 2;
+  return LB_OK;
+}
+
+lb_status lb_slab_unpack(lb_ctx* c) {
+  Range range_("lb_slab_unpack");
+  if (lb_status s = slab_only(c, "lb_slab_unpack"); s != LB_OK) return s;
+  if (c->slab_phase != 2)
+    return fail(c, LB_ERR_INVALID_ARG, "call lb_slab_step_faces and lb_slab_step_interior first");
+  char* pops = (char*)c->box.pop[c->cfg.scheme == LB_PULL ? (c->t & 1) : 0];
+  const SlabFaces f = slab_faces(c->slab_case, (uint32_t)c->slab_nz);
+  cudaError_t e = launch_faces(c, pops, f.recv_below, f.recv_above, c->face[2], c->face[3], 0);
+  if (e != cudaSuccess) return cuda_fail(c, e, "unpacking slab faces");
+  c->slab_phase = 0;
   return LB_OK;
 }
 

@@ -25,9 +25,10 @@ LB_F64, LB_F32, LB_F16 = range(3)
 LB_PULL, LB_AA = range(2)
 LB_EQ_PRODUCT, LB_EQ_POLY2 = range(2)
 LB_KERNEL_AUTO, LB_KERNEL_DIRECT, LB_KERNEL_STAGED, LB_KERNEL_PERSISTENT, \
-    LB_KERNEL_PACKED = range(5)
+    LB_KERNEL_PACKED, LB_KERNEL_ROWS, LB_KERNEL_ADJ = range(7)
 KERNEL = {"auto": LB_KERNEL_AUTO, "direct": LB_KERNEL_DIRECT, "staged": LB_KERNEL_STAGED,
-          "persistent": LB_KERNEL_PERSISTENT, "packed": LB_KERNEL_PACKED}
+          "persistent": LB_KERNEL_PERSISTENT, "packed": LB_KERNEL_PACKED,
+          "rows": LB_KERNEL_ROWS, "adj": LB_KERNEL_ADJ}
 
 STORAGE = {"f64": LB_F64, "f32": LB_F32, "f16": LB_F16}
 SCHEME = {"pull": LB_PULL, "aa": LB_AA}
@@ -87,7 +88,9 @@ SYMBOLS = ["lb_required_bytes", "lb_create", "lb_destroy", "lb_last_error", "lb_
            "lb_batch_last_error", "lb_batch_box", "lb_batch_step", "lb_batch_diagnostics",
            "lb_batch_autotune", "lb_batch_set_tile", "lb_batch_set_kernel",
            "lb_diagnostics_noalloc", "lb_stabilizer_gap", "lb_presolve", "lb_set_diag_order",
-           "lb_spectrum_work_bytes", "lb_spectrum"]
+           "lb_spectrum_work_bytes", "lb_spectrum", "lb_get_gamma", "lb_slab_required_bytes",
+           "lb_slab_create", "lb_slab_faces", "lb_slab_step_faces", "lb_slab_step_interior",
+           "lb_slab_unpack"]
 
 
 class LBError(RuntimeError):
@@ -126,6 +129,22 @@ def load(path: str = LIB_PATH):
         L.lb_diagnostics.argtypes = [vp, ctypes.POINTER(lb_diag)]
         L.lb_get_populations.restype = i32
         L.lb_get_populations.argtypes = [vp, vp, ctypes.c_int]
+        L.lb_get_gamma.restype = i32
+        L.lb_get_gamma.argtypes = [vp, vp, ctypes.c_int]
+        L.lb_slab_required_bytes.restype = ctypes.c_size_t
+        L.lb_slab_required_bytes.argtypes = [cfgp, i32]
+        L.lb_slab_create.restype = i32
+        L.lb_slab_create.argtypes = [cfgp, i32, i32, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]
+        L.lb_slab_faces.restype = i32
+        L.lb_slab_faces.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                    ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                    ctypes.POINTER(ctypes.c_size_t)]
+        L.lb_slab_step_faces.restype = i32
+        L.lb_slab_step_faces.argtypes = [vp, i32]
+        L.lb_slab_step_interior.restype = i32
+        L.lb_slab_step_interior.argtypes = [vp]
+        L.lb_slab_unpack.restype = i32
+        L.lb_slab_unpack.argtypes = [vp]
         L.lb_set_populations.restype = i32
         L.lb_set_populations.argtypes = [vp, vp, ctypes.c_int]
         L.lb_time.restype = i64
@@ -290,6 +309,43 @@ def lb_stabilizer_gap(ctx) -> lb_gap:
 
 def lb_get_populations(ctx, f_ptr: int, on_device: bool):
     _check(load().lb_get_populations(ctx, ctypes.c_void_p(f_ptr), int(on_device)), ctx)
+
+
+def lb_get_gamma(ctx, gamma_ptr: int, on_device: bool):
+    _check(load().lb_get_gamma(ctx, ctypes.c_void_p(gamma_ptr), int(on_device)), ctx)
+
+
+def lb_slab_required_bytes(cfg: lb_config, nz_local: int) -> int:
+    return int(load().lb_slab_required_bytes(ctypes.byref(cfg), int(nz_local)))
+
+
+def lb_slab_create(cfg: lb_config, z0: int, nz_local: int, dev_buf: int, nbytes: int,
+                   stream: int = 0):
+    out = ctypes.c_void_p()
+    _check(load().lb_slab_create(ctypes.byref(cfg), int(z0), int(nz_local),
+                                 ctypes.c_void_p(dev_buf), nbytes, ctypes.c_void_p(stream),
+                                 ctypes.byref(out)))
+    return out
+
+
+def lb_slab_faces(ctx):
+    """(send_up, send_down, recv_below, recv_above) device addresses and the face size."""
+    p = [ctypes.c_void_p() for _ in range(4)]
+    n = ctypes.c_size_t()
+    _check(load().lb_slab_faces(ctx, *[ctypes.byref(x) for x in p], ctypes.byref(n)), ctx)
+    return [x.value for x in p], n.value
+
+
+def lb_slab_step_faces(ctx, record: bool = False):
+    _check(load().lb_slab_step_faces(ctx, int(bool(record))), ctx)
+
+
+def lb_slab_step_interior(ctx):
+    _check(load().lb_slab_step_interior(ctx), ctx)
+
+
+def lb_slab_unpack(ctx):
+    _check(load().lb_slab_unpack(ctx), ctx)
 
 
 def lb_set_populations(ctx, f_ptr: int, on_device: bool):
@@ -528,6 +584,12 @@ class Lattice:
         f = np.empty((27,) + self.shape)
         lb_get_populations(self.ctx, f.ctypes.data, False)
         return f
+
+    def gamma(self) -> np.ndarray:
+        """The stabilizer of every node in the last collision (FP32, [nz, ny, nx])."""
+        g = np.empty(self.shape, dtype=np.float32)
+        lb_get_gamma(self.ctx, g.ctypes.data, False)
+        return g
 
     def set_populations(self, f):
         f = np.ascontiguousarray(f, dtype=np.float64)

@@ -105,7 +105,7 @@ def test_binding_structs_and_enums_match_the_header(tmp_path):
              "LB_S_CD", "LB_S_CDT", "LB_S_CDQ", "LB_S_CDTQ", "LB_GAMMA_ESTIMATE", "LB_GAMMA_LBGK",
              "LB_GAMMA_RLB", "LB_GAMMA_EXACT", "LB_F64", "LB_F32", "LB_F16", "LB_PULL", "LB_AA",
              "LB_EQ_PRODUCT", "LB_EQ_POLY2", "LB_KERNEL_AUTO", "LB_KERNEL_DIRECT",
-             "LB_KERNEL_STAGED", "LB_KERNEL_PERSISTENT", "LB_KERNEL_PACKED"]
+             "LB_KERNEL_STAGED", "LB_KERNEL_PERSISTENT", "LB_KERNEL_PACKED", "LB_KERNEL_ROWS", "LB_KERNEL_ADJ"]
     lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "kbc_lb.h"',
              "int main(void) {"]
     for name, cls in structs.items():

@@ -201,6 +201,82 @@ def test_all_step_kernels_are_bitwise_identical(kbc, storage, scheme, shape):
         assert np.max(np.abs(packed - out[0])) <= tol
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("scheme", ["pull", "aa"])
+@pytest.mark.parametrize("shape", [(256, 5, 3), (64, 8, 5), (32, 16, 3), (128, 6, 4),
+                                   (96, 4, 3), (24, 8, 3), (512, 3, 3), (768, 3, 3)])
+@pytest.mark.parametrize("steps", [4, 5])
+def test_two_node_kernels_match_bitwise(kbc, storage, scheme, shape, steps):
+    """The row-staged kernel (whole rows of R x nx nodes, or 256-node segments with halos;
+    tiles that wrap in y; odd and even AA steps) and the adjacent-pair kernel compute the same
+    FP32x2 collision as the packed kernel, only on other node pairs, so the three agree bit for
+    bit; all stay within the oracle tolerance."""
+    f0 = seeded_state(*shape, seed=21)
+    out = []
+    for kind in ("packed", "rows", "adj"):
+        lat = lattice(shape, storage=storage, scheme=scheme)
+        lat.set_kernel(kind)
+        lat.set_populations(f0)
+        lat.step(steps)
+        out.append(lat.get_populations())
+    assert np.array_equal(out[0], out[1])
+    assert np.array_equal(out[0], out[2])
+    ref, _, _ = oracle.run(f0, steps, oracle.beta(1e-3))
+    tol = {"f32": 1e-6, "f16": 2e-3}[storage]
+    assert np.max(np.abs(out[1] - ref)) <= tol
+
+
+def test_rows_kernel_rejects_shapes_it_does_not_take(kbc):
+    for shape in [(100, 8, 8), (200, 4, 4), (64, 7, 3), (40, 3, 3), (300, 3, 3)]:
+        lat = lattice(shape, storage="f32", scheme="aa")
+        with pytest.raises(lb.LBError) as e:
+            lat.set_kernel("rows")
+        assert e.value.status == lb.LB_ERR_UNSUPPORTED
+    lat64 = lattice((256, 3, 3), storage="f64", scheme="aa")
+    with pytest.raises(lb.LBError):
+        lat64.set_kernel("rows")
+    latc = lattice((256, 3, 3), storage="f32", scheme="aa", variant="cd+ct+cq")
+    with pytest.raises(lb.LBError):
+        latc.set_kernel("rows")
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("kind", ["direct", "packed", "rows", "adj"])
+def test_fp64_denominator_fallback_near_equilibrium(kbc, storage, kind):
+    """Populations 1e-7 (relative) away from equilibrium. In FP32 storage <dh|dh> ~ 1e-14 is
+    under the 1e-9 threshold at every node, so each node is collided in FP64 from its stored
+    inputs: its gamma equals the oracle's gamma of the same stored state to the FP32 rounding
+    of gamma (in FP32 arithmetic dh would carry a relative error of order 1 at this size), and
+    its populations are the FP64 collision rounded to FP32. FP16 storage rounds the 1e-7 away
+    (its half quantum is ~2e-5 relative), leaving <dh|dh> around the threshold: nodes on
+    either side, gamma within 1e-3. A state 1e-3 away stays on the FP32 collision; there gamma
+    agrees to 1e-3."""
+    n, nu = 24, 2e-4
+    rho, u = workloads.random_spectrum(n, 4, 0.04, seed=4)
+    feq = oracle.init_equilibrium(rho, u)
+    near_tol = 1e-6 if storage == "f32" else 1e-3
+    for noise, tol in ((1e-7, near_tol), (1e-3, 1e-3)):
+        f0 = feq * (1 + noise * workloads.population_noise(n, n, n, 8))
+        lat = lattice((n, n, n), nu=nu, storage=storage, scheme="aa")
+        lat.set_kernel(kind)
+        lat.set_populations(f0)
+        f_in = lat.get_populations()             # the stored (rounded) inputs
+        lat.step(1)
+        g_gpu = lat.gamma().astype(np.float64)
+        fo, g_ref, guarded = oracle.collide_field(f_in, lat.beta, want_gamma=True)
+        err = np.abs(g_gpu - g_ref) / np.maximum(np.abs(g_ref), 1.0)
+        assert np.max(err) <= tol, (noise, float(np.max(err)))
+        assert lat.diagnostics()["den_guard_count"] == guarded == 0
+        if noise == 1e-7 and storage == "f32":
+            expect = oracle.stream(fo)
+            expect = W4 + (expect - W4).astype(np.float32).astype(np.float64)
+            got = lat.get_populations()
+            # equal, or one FP32 ulp of the shift apart where the two FP64 collisions (same
+            # inputs, different operation order) straddle a rounding boundary
+            assert np.max(np.abs(got - expect)) <= 4e-9
+            assert np.mean(got == expect) > 0.99
+
+
 @pytest.mark.parametrize("variant", ["cd", "cd+ct+cq"])
 @pytest.mark.parametrize("scheme", ["pull", "aa"])
 @pytest.mark.parametrize("kind", ["direct", "packed"])
@@ -279,14 +355,15 @@ def test_packed_kernel_on_ragged_rows(kbc, storage, scheme, shape):
     assert d["nonfinite_count"] == 0
 
 
-def test_bounded_wait_reports_timeout_and_context_recovers(kbc):
-    """Test hook: the staged kernel issues no copies, so its first bounded wait runs out. The
+@pytest.mark.parametrize("kind", ["staged", "rows"])
+def test_bounded_wait_reports_timeout_and_context_recovers(kbc, kind):
+    """Test hook: the staged kernels issue no copies, so their first bounded wait runs out. The
     kernel returns, the next synchronising call reports LB_ERR_TIMEOUT, and the context keeps
     working once the hook is off."""
     shape = (64, 8, 8)
     f0 = seeded_state(*shape)
     lat = lattice(shape, storage="f32", scheme="pull")
-    lat.set_kernel("staged")
+    lat.set_kernel(kind)
     lat.set_populations(f0)
     lb.lb_set_wait_budget(lat.ctx, 200000, True)     # ~0.1 ms at 2 GHz
     lat.step(1)
@@ -342,7 +419,7 @@ def one_step_reference(lat):
 
 
 @pytest.mark.parametrize("scheme", ["pull", "aa"])
-@pytest.mark.parametrize("kind", ["direct", "packed"])
+@pytest.mark.parametrize("kind", ["direct", "packed", "rows", "adj"])
 def test_fp32_one_step_parity(kbc, scheme, kind):
     n = 24
     rho, u = workloads.random_spectrum(n, 4, 0.04, seed=1)
@@ -357,7 +434,7 @@ def test_fp32_one_step_parity(kbc, scheme, kind):
 
 
 @pytest.mark.parametrize("scheme", ["pull", "aa"])
-@pytest.mark.parametrize("kind", ["direct", "packed"])
+@pytest.mark.parametrize("kind", ["direct", "packed", "rows", "adj"])
 def test_fp16_one_step_parity_within_one_half_ulp(kbc, scheme, kind):
     n = 24
     rho, u = workloads.random_spectrum(n, 4, 0.04, seed=2)

@@ -17,11 +17,12 @@ V, W = oracle.lattice()
 
 @pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
 @pytest.mark.parametrize("scheme", ["pull", "aa"])
-@pytest.mark.parametrize("kind", ["direct", "packed", "staged", "persistent"])
+@pytest.mark.parametrize("kind", ["direct", "packed", "staged", "persistent", "rows", "adj"])
 # the packed kernel takes blocks of whole rows for nx = 128, 256, 512 (2, 4 and 2 x 4 warps)
-# and blocks of consecutive nodes straddling rows for the others
+# and blocks of consecutive nodes straddling rows for the others; the rows kernel takes tiles
+# of 4, 2 and 1 whole rows for nx = 64, 128 (ny = 4), 256 and 256-node segments for 512
 @pytest.mark.parametrize("shape", [(10, 9, 8), (37, 5, 4), (3, 3, 3), (300, 3, 4), (128, 3, 5),
-                                   (256, 4, 3), (512, 3, 3)])
+                                   (256, 4, 3), (512, 3, 3), (64, 4, 3), (128, 4, 3)])
 @pytest.mark.parametrize("steps", [1, 4, 7])
 def test_streaming_is_an_exact_permutation(kbc, storage, scheme, kind, shape, steps):
     nx, ny, nz = shape
