@@ -237,10 +237,10 @@ double lb_beta(const lb_ctx *ctx);
  * lb_set_populations). t >= 0. */
 lb_status lb_set_time(lb_ctx *ctx, int64_t t);
 
-/* Which step kernel runs. The one-node-per-thread kernels (direct, staged, persistent) give
- * bit-identical populations, and so do the two-nodes-per-thread kernels (packed, rows) among
- * themselves; the two families agree to FP32 round-off (the FP32x2 instructions round some
- * operations differently from their scalar forms). FP64 storage runs the direct kernel.
+/* Which step kernel runs. All kernels give bit-identical populations for a given storage
+ * (the FP32 kernels of one node per thread run the FP32x2 collision with the node in both
+ * lanes, so every FP32 kernel executes the same compiled arithmetic). FP64 storage runs the
+ * direct kernel.
  *   LB_KERNEL_ROWS        two adjacent nodes per thread on packed FP32x2 instructions; a
  *                         persistent grid walks tiles of whole rows (nx <= 256) or 256-node
  *                         row segments (nx a multiple of 256), whose 27 source rows the

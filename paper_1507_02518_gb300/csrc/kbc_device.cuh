@@ -1026,7 +1026,24 @@ __device__ __forceinline__ R collide_step(R (&d)[27], const CollideParams& cp, i
   using O = Ar<R>;
   using T = typename O::Scalar;
   if constexpr (!CENTRAL && !EXACT && !POLY && std::is_same<T, float>::value) {
-    return collide_lean<R, REL>(d, cp, guarded, fp64);
+    if constexpr (std::is_same<R, float>::value) {
+      // One node: the FP32x2 collision with the node in both lanes. Every FP32 step kernel
+      // then runs the same compiled arithmetic and gives the same bits; the scalar (float)
+      // instantiation rounds differently (the compiler places the approximate MUFU reciprocal
+      // and square root differently in the two code shapes).
+      float2 d2[27];
+#pragma unroll
+      for (int i = 0; i < 27; ++i) d2[i] = make_float2(d[i], d[i]);
+      int g2 = 0, f2 = 0;
+      const float2 gam = collide_lean<float2, REL>(d2, cp, &g2, fp64 ? &f2 : nullptr);
+#pragma unroll
+      for (int i = 0; i < 27; ++i) d[i] = d2[i].x;
+      *guarded = g2 & 1;
+      if (fp64) *fp64 = f2 & 1;
+      return gam.x;
+    } else {
+      return collide_lean<R, REL>(d, cp, guarded, fp64);
+    }
   } else {
     if constexpr (REL) {
 #pragma unroll
