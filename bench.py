@@ -532,7 +532,8 @@ def main_ours(args, rank, world, local):
     rl = roofline(w["storage"], kernel_mlups, peak, peak_kind,
                   None if traffic is None else traffic * res["P"])
     rl["kernel"] = "kbc::%s<%s, %s>" % (
-        "step_kernel" if w["storage"] == "f64" else "pair_step_kernel",
+        "step_kernel" if w["storage"] == "f64" else
+        ("adj_step_kernel" if w["n"] % 2 == 0 else "pair_step_kernel"),
         {"f64": "double", "f32": "float", "f16": "uint16 (half bits)"}[w["storage"]],
         "MODE_PULL" if w["scheme"] == "pull" else "MODE_AA_EVEN/ODD")
     rl["kernel_ms"] = round(kernel_ms, 5)

@@ -222,7 +222,7 @@ lb_status lb_get_populations(lb_ctx *ctx, double *f, int on_device);
 /* The stabilizer gamma of every node from the last collision of the last lb_step call
  * (eq:result21, or 2 / 1/beta in the LBGK / RLB modes; 2 where <dh|dh> fell under the guard;
  * FP32, caller-owned gamma[P], node order). An FP32-arithmetic collision takes the value of
- * its FP64 re-evaluation where its <dh|dh> fell under 1e-9. LB_ERR_INVALID_ARG when no step
+ * its FP64 re-evaluation where its <dh|dh> fell under 1e-13. LB_ERR_INVALID_ARG when no step
  * has run since the state was set. Synchronises. */
 lb_status lb_get_gamma(lb_ctx *ctx, float *gamma, int on_device);
 

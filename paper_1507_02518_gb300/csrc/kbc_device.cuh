@@ -201,11 +201,14 @@ template <> struct Guard<float> { static constexpr float den = 1e-30f; };
 
 // An FP32 collision whose <dh|dh> falls under kDenFp64 is not used: the lane is flagged
 // (*fp64 bit k), its populations are not stored, and the step kernel collides that node again
-// in FP64 from its stored inputs (fp64_node_update), with the FP64 guard of the oracle. Below
-// kDenFp64, dh is within about a thousand FP32 round-offs of the shifts it is the difference
-// of, so an FP32 <dh|dh> -- and the ratio of eq:result21 -- would carry that error; an
-// accurate denominator needs dh, and so the node's moments and equilibrium, in FP64.
-constexpr float kDenFp64 = 1e-9f;
+// in FP64 from its stored inputs (fp64_node_update), with the FP64 guard of the oracle. The
+// FP32 dh carries an absolute error of about 1e-8 (relative to W_i): the round-off of the
+// O(0.1) shifts it is the difference of. At <dh|dh> = 1e-13, |dh / W| ~ 3e-7, so the FP32
+// denominator -- and the ratio of eq:result21 -- would be off by a few per cent below it, while
+// at 1e-9 they are still good to 1e-3 (smooth fields at 512^3 have many nodes there, and
+// collide them in FP32). An accurate denominator needs dh, and so the node's moments and
+// equilibrium, in FP64.
+constexpr float kDenFp64 = 1e-13f;
 
 enum { GAMMA_ESTIMATE = 0, GAMMA_LBGK = 1, GAMMA_RLB = 2, GAMMA_EXACT = 3 };
 

@@ -245,17 +245,17 @@ def test_rows_kernel_rejects_shapes_it_does_not_take(kbc):
 @pytest.mark.parametrize("kind", ["direct", "packed", "rows", "adj"])
 def test_fp64_denominator_fallback_near_equilibrium(kbc, storage, kind):
     """Populations 1e-7 (relative) away from equilibrium. In FP32 storage <dh|dh> ~ 1e-14 is
-    under the 1e-9 threshold at every node, so each node is collided in FP64 from its stored
+    under the 1e-13 threshold at every node, so each node is collided in FP64 from its stored
     inputs: its gamma equals the oracle's gamma of the same stored state to the FP32 rounding
-    of gamma (in FP32 arithmetic dh would carry a relative error of order 1 at this size), and
-    its populations are the FP64 collision rounded to FP32. FP16 storage rounds the 1e-7 away
-    (its half quantum is ~2e-5 relative), leaving <dh|dh> around the threshold: nodes on
-    either side, gamma within 1e-3. A state 1e-3 away stays on the FP32 collision; there gamma
-    agrees to 1e-3."""
+    of gamma (in FP32 arithmetic dh would carry a relative error of order 0.1 at this size),
+    and its populations are the FP64 collision rounded to FP32. FP16 storage rounds the 1e-7
+    away (its half quantum is ~2e-5 relative), leaving <dh|dh> of 1e-11 .. 1e-9 from the
+    rounding: FP32 collisions whose gamma is within a few per cent of the oracle's. A state 1e-3
+    away stays on the FP32 collision; there gamma agrees to 1e-3."""
     n, nu = 24, 2e-4
     rho, u = workloads.random_spectrum(n, 4, 0.04, seed=4)
     feq = oracle.init_equilibrium(rho, u)
-    near_tol = 1e-6 if storage == "f32" else 1e-3
+    near_tol = 1e-6 if storage == "f32" else 5e-2
     for noise, tol in ((1e-7, near_tol), (1e-3, 1e-3)):
         f0 = feq * (1 + noise * workloads.population_noise(n, n, n, 8))
         lat = lattice((n, n, n), nu=nu, storage=storage, scheme="aa")
