@@ -308,10 +308,18 @@ def run_batch(w, steps, warmup, rank=0, world=1):
     if world > 1:                                 # LPT shard of the ensemble, no exchange
         boxes, _ = sharding.shard_boxes(boxes, rank, world)
     batch = lb.Batch(boxes, storage=w["storage"], scheme=w["scheme"])
-    tune = batch.autotune(2)                      # on the rest state, before the fields
-    for k, b in enumerate(boxes):
-        rho, u = workloads.random_spectrum(b["n"], b["k0"], b["urms"], b["seed"])
-        lb.lb_init_field(batch.box(k), 0, np.ascontiguousarray(u).ctypes.data, False)
+    fields = [np.ascontiguousarray(workloads.random_spectrum(b["n"], b["k0"], b["urms"],
+                                                             b["seed"])[1]) for b in boxes]
+
+    def init_fields():
+        for k in range(len(boxes)):
+            lb.lb_init_field(batch.box(k), 0, fields[k].ctypes.data, False)
+
+    # tuned on the initial fields (at rest every FP32 node would take the FP64 re-collision),
+    # which are then set again
+    init_fields()
+    tune = batch.autotune(2)
+    init_fields()
     batch.step(warmup)
     torch.cuda.synchronize()
     st = batch.stream

@@ -221,9 +221,11 @@ lb_status lb_get_populations(lb_ctx *ctx, double *f, int on_device);
 
 /* The stabilizer gamma of every node from the last collision of the last lb_step call
  * (eq:result21, or 2 / 1/beta in the LBGK / RLB modes; 2 where <dh|dh> fell under the guard;
- * FP32, caller-owned gamma[P], node order). An FP32-arithmetic collision takes the value of
- * its FP64 re-evaluation where its <dh|dh> fell under 1e-13. LB_ERR_INVALID_ARG when no step
- * has run since the state was set. Synchronises. */
+ * FP32, caller-owned gamma[P], node order). With LB_F32 storage, a node whose FP32 <dh|dh>
+ * fell under 1e-13 is collided again in FP64 from its inputs (a second kernel after each
+ * step kernel) and takes that gamma and those populations; LB_F16 storage keeps the FP32
+ * collision there. LB_ERR_INVALID_ARG when no step has run since the state was set.
+ * Synchronises. */
 lb_status lb_get_gamma(lb_ctx *ctx, float *gamma, int on_device);
 
 /* Overwrite the state with canonical populations f[27][P] at the current time t (checkpoint
@@ -378,19 +380,24 @@ lb_ctx *lb_batch_box(lb_batch *b, int32_t box);
 lb_status lb_batch_step(lb_batch *b, int64_t n);
 /* Diagnostics of every box into out[nbox]. Synchronises. */
 lb_status lb_batch_diagnostics(lb_batch *b, lb_diag *out);
-/* Kernel of the batched step: LB_KERNEL_PACKED (two nodes per thread on FP32x2 instructions,
- * 128 threads per block; LB_F32 / LB_F16), LB_KERNEL_DIRECT (one node per thread), or
- * LB_KERNEL_AUTO (default: packed when the arithmetic is FP32). */
+/* Kernel of the batched step, all with the same bits per storage type: LB_KERNEL_ADJ (two
+ * adjacent nodes (x, x+1) per thread on FP32x2 instructions, 128 threads per block; LB_F32 /
+ * LB_F16, every box with an even nx, natural moments; else LB_ERR_UNSUPPORTED),
+ * LB_KERNEL_PACKED (nodes (n, n+32) of an item per thread on FP32x2 instructions, 128 threads
+ * per block; LB_F32 / LB_F16), LB_KERNEL_DIRECT (one node per thread), or LB_KERNEL_AUTO
+ * (default: ADJ where it applies, else PACKED when the arithmetic is FP32, else DIRECT). */
 lb_status lb_batch_set_kernel(lb_batch *b, int32_t kind);
 /* Launch shape of the batched step: `threads` per block (multiple of 32, <= 512; 128 for the
- * packed kernel) and `tile`,
+ * ADJ and PACKED kernels) and `tile`,
  * the target number of nodes per work item (an item is ceil(tile / nx) whole x-rows of one
  * box). The grid is persistent: SMs x resident blocks, clamped to the number of items. */
 lb_status lb_batch_set_tile(lb_batch *b, int32_t threads, int32_t tile);
 /* Time each candidate (threads in {128, 256, 512}) x (tile in {256 .. 4096}) for
  * `trial_steps` steps on the current state and keep the fastest. The state advances by the
- * trial steps, so call it on a throw-away state (e.g. right after create) and initialise
- * afterwards. Outputs may be NULL; best_ms is the best time per step. Synchronises. */
+ * trial steps, so call it on a throw-away state like the one to be run (e.g. the initial
+ * fields) and initialise again afterwards. Not on the rest state with LB_F32 storage: there
+ * every node's <dh|dh> is 0 and takes the FP64 re-collision, which would be timed instead.
+ * Outputs may be NULL; best_ms is the best time per step. Synchronises. */
 lb_status lb_batch_autotune(lb_batch *b, int32_t trial_steps, int32_t *best_threads,
                             int32_t *best_tile, double *best_ms);
 

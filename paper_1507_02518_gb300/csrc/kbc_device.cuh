@@ -199,9 +199,15 @@ template <typename R> struct Guard;
 template <> struct Guard<double> { static constexpr double den = 1e-300; };
 template <> struct Guard<float> { static constexpr float den = 1e-30f; };
 
-// An FP32 collision whose <dh|dh> falls under kDenFp64 is not used: the lane is flagged
-// (*fp64 bit k), its populations are not stored, and the step kernel collides that node again
-// in FP64 from its stored inputs (fp64_node_update), with the FP64 guard of the oracle. The
+// With FP32 storage, an FP32 collision whose <dh|dh> falls under kDenFp64 is not used: the
+// lane is flagged (*fp64 bit k), the node's bit is set in the box's mask (flag_fp64), and a
+// pass launched after the step kernel (fp64_pass_kernel) collides the node again in FP64
+// from its inputs (fp64_node_update), with the FP64 guard of the oracle. The inputs are still
+// in memory then: the pull step reads src only and stores the flagged node's FP32 outputs
+// anyway (the pass overwrites them), the AA step does not store a flagged node (each AA node
+// alone reads and writes its slots). The step kernels hold no call of the FP64 path, which
+// would cost them registers. FP16 storage takes no FP64 path: its rounding of the stored
+// populations (the step's output) exceeds the FP32 error of gamma near equilibrium. The
 // FP32 dh carries an absolute error of about 1e-8 (relative to W_i): the round-off of the
 // O(0.1) shifts it is the difference of. At <dh|dh> = 1e-13, |dh / W| ~ 3e-7, so the FP32
 // denominator -- and the ratio of eq:result21 -- would be off by a few per cent below it, while
@@ -1098,8 +1104,19 @@ enum { MODE_PULL = 0, MODE_AA_EVEN = 1, MODE_AA_ODD = 2 };
 struct Geo {
   uint32_t nx, ny, nz, nxy;
   uint64_t P;
-  uint32_t zb, ze;  // the step kernels update the planes zb <= z < ze (all: 0, nz)
+  uint32_t zb, ze;         // the step kernels update the planes zb <= z < ze (all: 0, nz)
+  uint32_t* fbmask;        // one bit per node (linear index): collide again in FP64
+  unsigned int* fb_any;    // set to 1 with any bit of fbmask
+  unsigned int* fb_batch;  // the batch-wide flag, set as well (null outside a batch)
 };
+
+// Marks node n (linear index x + nx y + nx ny z) for the FP64 re-collision pass; the caller
+// has not stored its FP32 outputs.
+__device__ __forceinline__ void flag_fp64(const Geo& g, uint32_t n) {
+  atomicOr(g.fbmask + (n >> 5), 1u << (n & 31));
+  *g.fb_any = 1u;
+  if (g.fb_batch) *g.fb_batch = 1u;
+}
 
 // in-plane offsets of the 3x3x3 neighbourhood of (x, y, z) on the periodic box
 struct Nbr {
@@ -1150,12 +1167,11 @@ template <int N> struct Unroll<N, N> {
   template <typename F> __device__ __forceinline__ static void run(F&&) {}
 };
 
-// FP64 collision of one node whose FP32 <dh|dh> fell under kDenFp64: loads the node's inputs
-// where the step's pattern keeps them (the step stores a node's slots only after its
-// collision, and has not stored this node), collides them in FP64 (collide<double>, with the
-// oracle's guard) and stores the outputs in the storage type. Returns gamma; *guarded is set
-// when <dh|dh> fell under the FP64 guard. Called outside the FP32 collision, with little live,
-// so that the call does not weigh on the FP32 kernels' registers.
+// FP64 collision of one node whose FP32 <dh|dh> fell under kDenFp64, after the step kernel:
+// loads the node's inputs where the step's pattern keeps them (pull: src, which the step
+// does not write; AA: the node's own slots, which the step left alone), collides them in
+// FP64 (collide<double>, with the oracle's guard) and stores the outputs in the storage type.
+// Returns gamma; *guarded is set when <dh|dh> fell under the FP64 guard.
 template <typename S, int MODE, bool CENTRAL, bool POLY>
 __device__ __noinline__ float fp64_node_update(const S* src, S* dst, Geo g, uint32_t x,
                                                uint32_t y, uint32_t z, CollideParams cp,
@@ -1206,16 +1222,15 @@ __device__ __forceinline__ void node_update(const S* src, S* dst, const Geo& g, 
   });
   int guarded, fp64 = 0;
   R gamma = collide_step<R, CENTRAL, EXACT, POLY, C::rel>(
-      d, cp, &guarded, std::is_same<R, float>::value ? &fp64 : nullptr);
-  if (!fp64) {
+      d, cp, &guarded, std::is_same<S, float>::value ? &fp64 : nullptr);
+  if (MODE == MODE_PULL || !fp64) {  // a flagged node is left to the FP64 pass (AA: not stored)
     Unroll<0, 27>::run([&](auto ic) {
       constexpr int I = decltype(ic)::value;
       S* p = dst + (uint64_t)Pat::store_plane(I) * g.P + nb.template at<I, Pat::store_shift>();
       C::template store_raw<I>(p, d[I]);
     });
-  } else {
-    gamma = (R)fp64_node_update<S, MODE, CENTRAL, POLY>(src, dst, g, x, y, z, cp, &guarded);
   }
+  if (fp64) flag_fp64(g, nb.ox[1] + nb.oy[1] + nb.oz[1]);
   if constexpr (RECORD) {
     gamma_out[nb.ox[1] + nb.oy[1] + nb.oz[1]] = (float)gamma;
     if (guarded) atomicAdd(&ctr->guarded, 1ull);
@@ -1253,8 +1268,11 @@ __device__ __forceinline__ void node_update2(const S* src, S* dst, const Geo& g,
         base + na.template at<I, Pat::load_shift>(), base + nb.template at<I, Pat::load_shift>());
   });
   int guarded, fp64 = 0;
-  float2 gamma = collide_step<float2, CENTRAL, false, POLY, C::rel>(d, cp, &guarded, &fp64);
-  const bool va = !(fp64 & 1), vbs = vb && !(fp64 & 2);
+  float2 gamma = collide_step<float2, CENTRAL, false, POLY, C::rel>(
+      d, cp, &guarded, std::is_same<S, float>::value ? &fp64 : nullptr);
+  // flagged lanes are left to the FP64 pass (AA: not stored)
+  const bool va = MODE == MODE_PULL || !(fp64 & 1);
+  const bool vbs = vb && (MODE == MODE_PULL || !(fp64 & 2));
   // In the AA modes the stores reuse the load addresses' planes; opaque copies of P and dst
   // make the compiler recompute the store addresses instead of keeping 27 64-bit addresses
   // live across the collision (which spilled at 3 blocks per SM).
@@ -1283,16 +1301,9 @@ __device__ __forceinline__ void node_update2(const S* src, S* dst, const Geo& g,
     Codec2<S>::template store<I>(base + sa.template at<I, Pat::store_shift>(),
                                  base + sb.template at<I, Pat::store_shift>(), va, vbs, d[I]);
   });
-  if (fp64) {  // lanes whose <dh|dh> fell under kDenFp64: FP64 collision of those nodes
-    int g64 = 0;
-    if (fp64 & 1) {
-      gamma.x = fp64_node_update<S, MODE, CENTRAL, POLY>(src, dst, g, xa, ya, za, cp, &g64);
-      guarded = (guarded & ~1) | g64;
-    }
-    if ((fp64 & 2) && vb) {
-      gamma.y = fp64_node_update<S, MODE, CENTRAL, POLY>(src, dst, g, xb, yb, zb, cp, &g64);
-      guarded = (guarded & ~2) | (g64 << 1);
-    }
+  if (fp64) {
+    if (fp64 & 1) flag_fp64(g, na.ox[1] + na.oy[1] + na.oz[1]);
+    if ((fp64 & 2) && vb) flag_fp64(g, nb.ox[1] + nb.oy[1] + nb.oz[1]);
   }
   if constexpr (RECORD) {
     gamma_out[na.ox[1] + na.oy[1] + na.oz[1]] = gamma.x;
@@ -1333,8 +1344,12 @@ __device__ __forceinline__ void node_update_adj(const S* src, S* dst, const Geo&
     d[I] = IO::template get<LS * cx(I), MODE == MODE_PULL>(row + x, row + xm, row + xp2);
   });
   int guarded, fp64 = 0;
-  float2 gamma = collide_step<float2, false, false, false, C::rel>(d, cp, &guarded, &fp64);
-  const bool wa = !(fp64 & 1), wb = !(fp64 & 2);
+  float2 gamma = collide_step<float2, false, false, false, C::rel>(
+      d, cp, &guarded, std::is_same<S, float>::value ? &fp64 : nullptr);
+  // flagged lanes are left to the FP64 pass; the pull step stores them anyway (the pass
+  // overwrites them from src), the AA step does not
+  const int skip = MODE == MODE_PULL ? 0 : fp64;
+  const bool wa = !(skip & 1), wb = !(skip & 2);
   // AA: opaque copies of P and dst keep the compiler from holding 27 addresses across the
   // collision
   uint64_t Ps = g.P;
@@ -1346,7 +1361,7 @@ __device__ __forceinline__ void node_update_adj(const S* src, S* dst, const Geo&
     S* row = dsts + (uint64_t)Pat::store_plane(I) * Ps + oy[SS * cy(I) + 1] + oz[SS * cz(I) + 1];
     constexpr int SX = SS * cx(I);
     if constexpr (SX == 0) {
-      if (!fp64) {
+      if (!skip) {
         IO::put2(row + x, d[I]);
       } else {
         if (wa) IO::put1(row + x, d[I].x);
@@ -1360,16 +1375,9 @@ __device__ __forceinline__ void node_update_adj(const S* src, S* dst, const Geo&
       if (wb) IO::put1(row + x, d[I].y);
     }
   });
-  if (fp64) {  // lanes whose <dh|dh> fell under kDenFp64: FP64 collision of those nodes
-    int g64 = 0;
-    if (fp64 & 1) {
-      gamma.x = fp64_node_update<S, MODE, false, false>(src, dst, g, x, y, z, cp, &g64);
-      guarded = (guarded & ~1) | g64;
-    }
-    if (fp64 & 2) {
-      gamma.y = fp64_node_update<S, MODE, false, false>(src, dst, g, x + 1, y, z, cp, &g64);
-      guarded = (guarded & ~2) | (g64 << 1);
-    }
+  if (fp64) {
+    if (fp64 & 1) flag_fp64(g, oy[1] + oz[1] + x);
+    if (fp64 & 2) flag_fp64(g, oy[1] + oz[1] + x + 1);
   }
   if constexpr (RECORD) {
     *reinterpret_cast<float2*>(gamma_out + oy[1] + oz[1] + x) = gamma;

@@ -144,34 +144,50 @@ static cudaError_t launch_pair(const S* src, S* dst, const Geo& g, const Collide
   return cudaGetLastError();
 }
 
+// the geometry and collision parameters of box `bd` of a batch (the whole box is stepped;
+// flagged nodes also set the batch-wide flag fb_batch)
+__device__ __forceinline__ Geo box_geo(const BoxDesc& bd, unsigned int* fb_batch) {
+  Geo g;
+  g.nx = bd.nx;
+  g.ny = bd.ny;
+  g.nz = bd.nz;
+  g.nxy = bd.nxy;
+  g.P = (uint64_t)bd.nxy * bd.nz;
+  g.zb = 0;
+  g.ze = bd.nz;
+  g.fbmask = bd.fbmask;
+  g.fb_any = &bd.ctr->fb_any;
+  g.fb_batch = fb_batch;
+  return g;
+}
+
+__device__ __forceinline__ CollideParams box_cp(const BoxDesc& bd, int with_t, int with_q,
+                                                int gamma_mode) {
+  CollideParams cp;
+  cp.beta = bd.beta;
+  cp.two_beta = bd.two_beta;
+  cp.inv_beta = bd.inv_beta;
+  cp.betaf = (float)bd.beta;
+  cp.two_betaf = (float)bd.two_beta;
+  cp.inv_betaf = (float)bd.inv_beta;
+  cp.with_t = with_t;
+  cp.with_q = with_q;
+  cp.gamma_mode = gamma_mode;
+  return cp;
+}
+
 // Batched ensemble: a persistent grid walks the work list; item k covers rows
 // [row0, row0 + nrows) (row = y + ny z) of one box.
 template <typename S, int MODE, bool RECORD, bool CENTRAL>
 __global__ void __launch_bounds__(MaxThreads<S>::value) batch_kernel(const BoxDesc* __restrict__ boxes,
                                                     const WorkItem* __restrict__ items,
-                                                    int nitems, int parity, int with_t,
-                                                    int with_q, int gamma_mode) {
+                                                    int nitems, BatchFlags* flags, int parity,
+                                                    int with_t, int with_q, int gamma_mode) {
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const WorkItem w = items[it];
     const BoxDesc bd = boxes[w.box];
-    Geo g;
-    g.nx = bd.nx;
-    g.ny = bd.ny;
-    g.nz = bd.nz;
-    g.nxy = bd.nxy;
-    g.P = (uint64_t)bd.nxy * bd.nz;
-    g.zb = 0;
-    g.ze = bd.nz;
-    CollideParams cp;
-    cp.beta = bd.beta;
-    cp.two_beta = bd.two_beta;
-    cp.inv_beta = bd.inv_beta;
-    cp.betaf = (float)bd.beta;
-    cp.two_betaf = (float)bd.two_beta;
-    cp.inv_betaf = (float)bd.inv_beta;
-    cp.with_t = with_t;
-    cp.with_q = with_q;
-    cp.gamma_mode = gamma_mode;
+    const Geo g = box_geo(bd, &flags->any);
+    const CollideParams cp = box_cp(bd, with_t, with_q, gamma_mode);
     const S* src = (const S*)bd.pop[MODE == MODE_PULL ? parity : 0];
     S* dst = (S*)bd.pop[MODE == MODE_PULL ? (parity ^ 1) : 0];
     const uint32_t nodes = bd.nx * (uint32_t)w.nrows;
@@ -190,29 +206,13 @@ __global__ void __launch_bounds__(MaxThreads<S>::value) batch_kernel(const BoxDe
 template <typename S, int MODE, bool RECORD, bool CENTRAL>
 __global__ void __launch_bounds__(128, 3) batch_pair_kernel(const BoxDesc* __restrict__ boxes,
                                                            const WorkItem* __restrict__ items,
-                                                           int nitems, int parity, int with_t,
-                                                           int with_q, int gamma_mode) {
+                                                           int nitems, BatchFlags* flags, int parity,
+                                                           int with_t, int with_q, int gamma_mode) {
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const WorkItem w = items[it];
     const BoxDesc bd = boxes[w.box];
-    Geo g;
-    g.nx = bd.nx;
-    g.ny = bd.ny;
-    g.nz = bd.nz;
-    g.nxy = bd.nxy;
-    g.P = (uint64_t)bd.nxy * bd.nz;
-    g.zb = 0;
-    g.ze = bd.nz;
-    CollideParams cp;
-    cp.beta = bd.beta;
-    cp.two_beta = bd.two_beta;
-    cp.inv_beta = bd.inv_beta;
-    cp.betaf = (float)bd.beta;
-    cp.two_betaf = (float)bd.two_beta;
-    cp.inv_betaf = (float)bd.inv_beta;
-    cp.with_t = with_t;
-    cp.with_q = with_q;
-    cp.gamma_mode = gamma_mode;
+    const Geo g = box_geo(bd, &flags->any);
+    const CollideParams cp = box_cp(bd, with_t, with_q, gamma_mode);
     const S* src = (const S*)bd.pop[MODE == MODE_PULL ? parity : 0];
     S* dst = (S*)bd.pop[MODE == MODE_PULL ? (parity ^ 1) : 0];
     // The item's rows are one contiguous range of nodes: warp q handles its nodes
@@ -238,6 +238,123 @@ __global__ void __launch_bounds__(128, 3) batch_pair_kernel(const BoxDesc* __res
   }
 }
 
+// The adjacent-pair form of the batched step (every box of the batch has an even nx; product
+// form, natural moments): each thread takes nodes (x, x + 1) of a row, x even, walking the
+// item's node range 256 nodes per block pass (coordinates advance incrementally).
+template <typename S, int MODE, bool RECORD>
+__global__ void __launch_bounds__(128, 3) batch_adj_kernel(const BoxDesc* __restrict__ boxes,
+                                                          const WorkItem* __restrict__ items,
+                                                          int nitems, BatchFlags* flags, int parity,
+                                                          int with_t, int with_q, int gamma_mode) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const WorkItem w = items[it];
+    const BoxDesc bd = boxes[w.box];
+    const Geo g = box_geo(bd, &flags->any);
+    const CollideParams cp = box_cp(bd, with_t, with_q, gamma_mode);
+    const S* src = (const S*)bd.pop[MODE == MODE_PULL ? parity : 0];
+    S* dst = (S*)bd.pop[MODE == MODE_PULL ? (parity ^ 1) : 0];
+    const uint32_t nodes = bd.nx * (uint32_t)w.nrows;
+    const uint32_t stride = 2 * blockDim.x;
+    uint32_t n = 2 * threadIdx.x;
+    uint32_t z = (uint32_t)w.row0 / bd.ny;
+    uint32_t y = (uint32_t)w.row0 - z * bd.ny, x = 0;
+    advance_node(x, y, z, n, bd.nx, bd.ny);
+    for (; n < nodes; n += stride) {
+      node_update_adj<S, MODE, RECORD>(src, dst, g, x, y, z, cp, bd.gamma, bd.ctr);
+      advance_node(x, y, z, stride, bd.nx, bd.ny);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ FP64 re-collision pass
+// A step kernel (FP32 storage) that meets a node whose FP32 <dh|dh> fell under kDenFp64 sets
+// its bit in the box's mask (flag_fp64) and, in AA, does not store it. The pass launched
+// after it collides every flagged node again in FP64 from its inputs (fp64_node_update) and
+// clears the mask. When nothing was flagged (the usual case) it
+// reads one flag and exits. The last of its blocks to finish clears the flags; all blocks
+// have read them by then.
+constexpr int kPassThreads = 256;
+constexpr int kPassBlocks = 152;  // one wave: the pass kernels run one block per SM
+
+// the flagged nodes among mask words w = w0, w0 + stride, ...; returns the guard events
+template <typename S, int MODE, bool CENTRAL, bool POLY>
+__device__ unsigned long long fp64_pass_words(const S* src, S* dst, const Geo& g,
+                                              const CollideParams& cp,
+                                              float* gamma_out, int record, uint32_t w0,
+                                              uint32_t stride) {
+  const uint32_t words = (uint32_t)((g.P + 31) >> 5);
+  unsigned long long guards = 0;
+  for (uint32_t w = w0; w < words; w += stride) {
+    uint32_t m = g.fbmask[w];
+    if (m == 0) continue;
+    g.fbmask[w] = 0;
+    while (m) {
+      const uint32_t n = 32 * w + (uint32_t)(__ffs(m) - 1);
+      m &= m - 1;
+      const uint32_t z = n / g.nxy, r = n - z * g.nxy;
+      const uint32_t y = r / g.nx, x = r - y * g.nx;
+      int gd = 0;
+      const float gam = fp64_node_update<S, MODE, CENTRAL, POLY>(src, dst, g, x, y, z, cp, &gd);
+      if (record) {
+        gamma_out[n] = gam;
+        guards += (unsigned long long)gd;
+      }
+    }
+  }
+  return guards;
+}
+
+// true in thread 0 of the last block of the grid to get here (after __syncthreads)
+__device__ __forceinline__ bool pass_last_block(unsigned int* done) {
+  __syncthreads();
+  if (threadIdx.x != 0) return false;
+  __threadfence();
+  return atomicAdd(done, 1u) == gridDim.x - 1;
+}
+
+template <typename S, int MODE, bool CENTRAL, bool POLY>
+__global__ void __launch_bounds__(kPassThreads) fp64_pass_kernel(const S* src, S* dst, Geo g,
+                                                                 CollideParams cp,
+                                                                 float* gamma_out,
+                                                                 StepCounters* ctr, int record) {
+  if (*(volatile unsigned int*)&ctr->fb_any == 0) return;
+  const unsigned long long guards =
+      fp64_pass_words<S, MODE, CENTRAL, POLY>(src, dst, g, cp, gamma_out, record,
+                                              blockIdx.x * blockDim.x + threadIdx.x,
+                                              gridDim.x * blockDim.x);
+  if (guards) atomicAdd(&ctr->guarded, guards);
+  if (pass_last_block(&ctr->fb_done)) {
+    ctr->fb_any = 0;
+    ctr->fb_done = 0;
+  }
+}
+
+// the same over the boxes of a batch (boxes that flagged nothing are skipped)
+template <typename S, int MODE, bool CENTRAL>
+__global__ void __launch_bounds__(kPassThreads) batch_fp64_pass_kernel(
+    const BoxDesc* __restrict__ boxes, int nbox, BatchFlags* flags, int parity, int with_t,
+    int with_q, int gamma_mode, int record) {
+  if (*(volatile unsigned int*)&flags->any == 0) return;
+  for (int k = 0; k < nbox; ++k) {
+    const BoxDesc bd = boxes[k];
+    if (*(volatile unsigned int*)&bd.ctr->fb_any == 0) continue;
+    const Geo g = box_geo(bd, nullptr);
+    const CollideParams cp = box_cp(bd, with_t, with_q, gamma_mode);
+    const S* src = (const S*)bd.pop[MODE == MODE_PULL ? parity : 0];
+    S* dst = (S*)bd.pop[MODE == MODE_PULL ? (parity ^ 1) : 0];
+    const unsigned long long guards =
+        fp64_pass_words<S, MODE, CENTRAL, false>(src, dst, g, cp, bd.gamma, record,
+                                                 blockIdx.x * blockDim.x + threadIdx.x,
+                                                 gridDim.x * blockDim.x);
+    if (guards) atomicAdd(&bd.ctr->guarded, guards);
+  }
+  if (pass_last_block(&flags->done)) {
+    for (int k = 0; k < nbox; ++k) boxes[k].ctr->fb_any = 0;
+    flags->any = 0;
+    flags->done = 0;
+  }
+}
+
 // ------------------------------------------------------------------ host launchers
 inline Geo make_geo(const BoxView& b) {
   Geo g;
@@ -248,6 +365,9 @@ inline Geo make_geo(const BoxView& b) {
   g.P = b.P;
   g.zb = b.zb;
   g.ze = b.ze;
+  g.fbmask = b.fbmask;
+  g.fb_any = nullptr;
+  g.fb_batch = nullptr;
   return g;
 }
 
@@ -312,18 +432,38 @@ static cudaError_t launch_step_c(const BoxView& b, const S* src, S* dst, const G
   return cudaGetLastError();
 }
 
+// the step kernel, then (FP32 storage, the estimate of eq:result21: the only case that
+// flags nodes) the FP64 re-collision pass over the nodes it flagged
+template <typename S, int MODE, bool RECORD, bool CENTRAL, bool POLY>
+static cudaError_t launch_step_p(const BoxView& b, const S* src, S* dst, const Geo& g,
+                                 const CollideParams& cp, const StepOpts& o, StepCounters* ctr,
+                                 cudaStream_t st) {
+  cudaError_t e = launch_step_c<S, MODE, RECORD, CENTRAL, POLY>(b, src, dst, g, cp, o, ctr, st);
+  if constexpr (std::is_same<S, float>::value) {
+    if (e == cudaSuccess && cp.gamma_mode == GAMMA_ESTIMATE) {
+      const uint64_t words = (g.P + 31) / 32;
+      uint64_t blocks = (words + kPassThreads - 1) / kPassThreads;
+      if (blocks > (uint64_t)kPassBlocks) blocks = kPassBlocks;
+      fp64_pass_kernel<S, MODE, CENTRAL, POLY><<<(unsigned)blocks, kPassThreads, 0, st>>>(
+          src, dst, g, cp, b.gamma, ctr, RECORD ? 1 : 0);
+      e = cudaGetLastError();
+    }
+  }
+  return e;
+}
+
 template <typename S, int MODE, bool RECORD>
 static cudaError_t launch_step(const BoxView& b, const S* src, S* dst, const Geo& g,
                                const CollideParams& cp, const StepOpts& o, StepCounters* ctr,
                                cudaStream_t st) {
   if (b.poly) {
     if (b.central)
-      return launch_step_c<S, MODE, RECORD, true, true>(b, src, dst, g, cp, o, ctr, st);
-    return launch_step_c<S, MODE, RECORD, false, true>(b, src, dst, g, cp, o, ctr, st);
+      return launch_step_p<S, MODE, RECORD, true, true>(b, src, dst, g, cp, o, ctr, st);
+    return launch_step_p<S, MODE, RECORD, false, true>(b, src, dst, g, cp, o, ctr, st);
   }
   if (b.central)
-    return launch_step_c<S, MODE, RECORD, true, false>(b, src, dst, g, cp, o, ctr, st);
-  return launch_step_c<S, MODE, RECORD, false, false>(b, src, dst, g, cp, o, ctr, st);
+    return launch_step_p<S, MODE, RECORD, true, false>(b, src, dst, g, cp, o, ctr, st);
+  return launch_step_p<S, MODE, RECORD, false, false>(b, src, dst, g, cp, o, ctr, st);
 }
 
 template <typename S>
@@ -344,6 +484,8 @@ bool Ops<S>::rows_ok(uint32_t nx, uint32_t ny, uint32_t nz) {
     g.P = (uint64_t)nx * ny * nz;
     g.zb = 0;
     g.ze = nz;
+    g.fbmask = nullptr;
+    g.fb_any = g.fb_batch = nullptr;
     RowsArgs a;
     return rows_shape<S>(g, &a);
   }
@@ -352,7 +494,8 @@ bool Ops<S>::rows_ok(uint32_t nx, uint32_t ny, uint32_t nz) {
 template <typename S>
 cudaError_t Ops<S>::step(const BoxView& b, int64_t t, bool record, const StepOpts& o,
                          StepCounters* counters, cudaStream_t st) {
-  const Geo g = make_geo(b);
+  Geo g = make_geo(b);
+  g.fb_any = &counters->fb_any;
   const CollideParams cp = make_cp(b.beta, b.with_t, b.with_q, b.gamma_mode);
   const int parity = (int)(t & 1);
   if (b.scheme == 0) {
@@ -369,64 +512,107 @@ cudaError_t Ops<S>::step(const BoxView& b, int64_t t, bool record, const StepOpt
                 : launch_step<S, MODE_AA_ODD, false>(b, buf, buf, g, cp, o, counters, st);
 }
 
+// Launch arguments shared by the batch kernels.
+struct BatchArgs {
+  const BoxDesc* boxes;
+  int nbox;
+  BatchFlags* flags;
+  const WorkItem* items;
+  int nitems, parity, with_t, with_q, gamma_mode, threads, grid;
+};
+
 template <typename S, int MODE, bool CENTRAL>
-static void launch_batch_c(const BoxDesc* boxes, const WorkItem* items, int nitems, int parity,
-                           bool record, bool packed, int with_t, int with_q, int gamma_mode,
-                           int threads, int grid, cudaStream_t st) {
+static void launch_batch_c(const BatchArgs& a, bool record, int packed, cudaStream_t st) {
   if constexpr (!std::is_same<S, double>::value) {
+    if constexpr (!CENTRAL) {
+      if (packed == 2) {
+        if (record)
+          batch_adj_kernel<S, MODE, true><<<a.grid, 128, 0, st>>>(
+              a.boxes, a.items, a.nitems, a.flags, a.parity, a.with_t, a.with_q, a.gamma_mode);
+        else
+          batch_adj_kernel<S, MODE, false><<<a.grid, 128, 0, st>>>(
+              a.boxes, a.items, a.nitems, a.flags, a.parity, a.with_t, a.with_q, a.gamma_mode);
+        return;
+      }
+    }
     if (packed) {
       if (record)
-        batch_pair_kernel<S, MODE, true, CENTRAL><<<grid, 128, 0, st>>>(
-            boxes, items, nitems, parity, with_t, with_q, gamma_mode);
+        batch_pair_kernel<S, MODE, true, CENTRAL><<<a.grid, 128, 0, st>>>(
+            a.boxes, a.items, a.nitems, a.flags, a.parity, a.with_t, a.with_q, a.gamma_mode);
       else
-        batch_pair_kernel<S, MODE, false, CENTRAL><<<grid, 128, 0, st>>>(
-            boxes, items, nitems, parity, with_t, with_q, gamma_mode);
+        batch_pair_kernel<S, MODE, false, CENTRAL><<<a.grid, 128, 0, st>>>(
+            a.boxes, a.items, a.nitems, a.flags, a.parity, a.with_t, a.with_q, a.gamma_mode);
       return;
     }
   }
   if (record)
-    batch_kernel<S, MODE, true, CENTRAL><<<grid, threads, 0, st>>>(boxes, items, nitems, parity,
-                                                                   with_t, with_q, gamma_mode);
+    batch_kernel<S, MODE, true, CENTRAL><<<a.grid, a.threads, 0, st>>>(
+        a.boxes, a.items, a.nitems, a.flags, a.parity, a.with_t, a.with_q, a.gamma_mode);
   else
-    batch_kernel<S, MODE, false, CENTRAL><<<grid, threads, 0, st>>>(boxes, items, nitems, parity,
-                                                                    with_t, with_q, gamma_mode);
+    batch_kernel<S, MODE, false, CENTRAL><<<a.grid, a.threads, 0, st>>>(
+        a.boxes, a.items, a.nitems, a.flags, a.parity, a.with_t, a.with_q, a.gamma_mode);
 }
 
 template <typename S, int MODE>
-static void launch_batch(const BoxDesc* boxes, const WorkItem* items, int nitems, int parity,
-                         bool record, bool packed, bool central, int with_t, int with_q,
-                         int gamma_mode, int threads, int grid, cudaStream_t st) {
+static void launch_batch(const BatchArgs& a, bool record, int packed, bool central,
+                         cudaStream_t st) {
   if (central)
-    launch_batch_c<S, MODE, true>(boxes, items, nitems, parity, record, packed, with_t, with_q,
-                                  gamma_mode, threads, grid, st);
+    launch_batch_c<S, MODE, true>(a, record, packed, st);
   else
-    launch_batch_c<S, MODE, false>(boxes, items, nitems, parity, record, packed, with_t, with_q,
-                                   gamma_mode, threads, grid, st);
+    launch_batch_c<S, MODE, false>(a, record, packed, st);
+  if constexpr (std::is_same<S, float>::value) {
+    if (a.gamma_mode == GAMMA_ESTIMATE) {  // the FP32 kernels' flagged nodes, in FP64
+      if (central)
+        batch_fp64_pass_kernel<S, MODE, true><<<kPassBlocks, kPassThreads, 0, st>>>(
+            a.boxes, a.nbox, a.flags, a.parity, a.with_t, a.with_q, a.gamma_mode, record);
+      else
+        batch_fp64_pass_kernel<S, MODE, false><<<kPassBlocks, kPassThreads, 0, st>>>(
+            a.boxes, a.nbox, a.flags, a.parity, a.with_t, a.with_q, a.gamma_mode, record);
+    }
+  }
 }
 
 template <typename S>
-cudaError_t Ops<S>::batch_step(const BoxDesc* boxes, const WorkItem* items, int nitems,
-                               int64_t t, bool record, bool packed, int scheme, int with_t,
-                               int with_q, int central, int gamma_mode, int threads, int grid,
-                               cudaStream_t st) {
-  const int parity = (int)(t & 1);
+cudaError_t Ops<S>::batch_step(const BoxDesc* boxes, int nbox, BatchFlags* flags,
+                               const WorkItem* items, int nitems, int64_t t, bool record,
+                               int packed, int scheme, int with_t, int with_q, int central,
+                               int gamma_mode, int threads, int grid, cudaStream_t st) {
+  BatchArgs a;
+  a.boxes = boxes;
+  a.nbox = nbox;
+  a.flags = flags;
+  a.items = items;
+  a.nitems = nitems;
+  a.parity = (int)(t & 1);
+  a.with_t = with_t;
+  a.with_q = with_q;
+  a.gamma_mode = gamma_mode;
+  a.threads = threads;
+  a.grid = grid;
   if (scheme == 0)
-    launch_batch<S, MODE_PULL>(boxes, items, nitems, parity, record, packed, central, with_t,
-                               with_q, gamma_mode, threads, grid, st);
-  else if (parity == 0)
-    launch_batch<S, MODE_AA_EVEN>(boxes, items, nitems, parity, record, packed, central, with_t,
-                                  with_q, gamma_mode, threads, grid, st);
+    launch_batch<S, MODE_PULL>(a, record, packed, central != 0, st);
+  else if (a.parity == 0)
+    launch_batch<S, MODE_AA_EVEN>(a, record, packed, central != 0, st);
   else
-    launch_batch<S, MODE_AA_ODD>(boxes, items, nitems, parity, record, packed, central, with_t,
-                                 with_q, gamma_mode, threads, grid, st);
+    launch_batch<S, MODE_AA_ODD>(a, record, packed, central != 0, st);
   return cudaGetLastError();
 }
 
 template <typename S>
-int Ops<S>::batch_occupancy(int threads, int scheme, bool packed) {
+int Ops<S>::batch_occupancy(int threads, int scheme, int packed) {
   int blocks = 0;
   cudaError_t e = cudaErrorInvalidValue;
   if constexpr (!std::is_same<S, double>::value) {
+    if (packed == 2) {
+      if (scheme == 0)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &blocks, batch_adj_kernel<S, MODE_PULL, false>, 128, 0);
+      else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &blocks, batch_adj_kernel<S, MODE_AA_ODD, false>, 128, 0);
+      if (e != cudaSuccess || blocks < 1) blocks = 1;
+      return blocks;
+    }
     if (packed) {
       if (scheme == 0)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(

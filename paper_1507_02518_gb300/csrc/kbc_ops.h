@@ -11,6 +11,8 @@ struct BoxView {
   uint64_t P;          // nx * ny * nz
   void* pop[2];        // population buffers (pull: two; AA: pop[1] == pop[0])
   float* gamma;        // [P] stabilizer of the last recorded collision
+  uint32_t* fbmask;    // [ceil(P / 32)] nodes flagged for the FP64 re-collision (zero between
+                       // steps)
   double beta;
   int with_t, with_q, gamma_mode;
   int central;         // shear part in the central-moment basis
@@ -19,12 +21,22 @@ struct BoxView {
   uint32_t zb, ze;     // planes zb <= z < ze are stepped (a whole box: 0, nz)
 };
 
-// counters written by the step kernels: guard events of the recorded collision, and a flag
-// set when a bounded device-side wait ran out
+// counters written by the step kernels: guard events of the recorded collision, a flag set
+// when a bounded device-side wait ran out, and the state of the FP64 re-collision pass
+// (fb_any: a step kernel flagged a node in fbmask; fb_done: blocks of the pass that finished)
 struct StepCounters {
   unsigned long long guarded;
   unsigned int timeout;
+  unsigned int fb_any;
+  unsigned int fb_done;
   unsigned int pad;
+};
+
+// the batch-wide flag of the FP64 re-collision pass (some box flagged a node) and its count
+// of finished blocks
+struct BatchFlags {
+  unsigned int any;
+  unsigned int done;
 };
 
 // kernel choice and test hooks of one step launch
@@ -59,6 +71,7 @@ struct BoxDesc {
   uint32_t nx, ny, nz, nxy;
   void* pop[2];
   float* gamma;
+  uint32_t* fbmask;
   StepCounters* ctr;
   double beta, two_beta, inv_beta;
 };
@@ -100,13 +113,16 @@ template <typename S> struct Ops {
   static cudaError_t gamma_gap(const BoxView& b, int64_t t, double* partials, int nblocks,
                                double* sums, cudaStream_t st);
   // one time step of every box of a batch over a work list
-  // (packed: the FP32x2 two-nodes-per-thread form, 128 threads; FP32 arithmetic only)
-  static cudaError_t batch_step(const BoxDesc* boxes, const WorkItem* items, int nitems,
-                                int64_t t, bool record, bool packed, int scheme, int with_t,
+  // (packed: 0 one node per thread; 1 the FP32x2 (n, n + 32) pairs, 128 threads; 2 the FP32x2
+  // adjacent pairs (x, x + 1), 128 threads, every nx even, natural moments; FP32 arithmetic)
+  // (flags: the batch's FP64 re-collision flag; nbox boxes)
+  static cudaError_t batch_step(const BoxDesc* boxes, int nbox, BatchFlags* flags,
+                                const WorkItem* items, int nitems,
+                                int64_t t, bool record, int packed, int scheme, int with_t,
                                 int with_q, int central, int gamma_mode, int threads, int grid,
                                 cudaStream_t st);
   // resident blocks per SM of the batch kernel at this block size
-  static int batch_occupancy(int threads, int scheme, bool packed);
+  static int batch_occupancy(int threads, int scheme, int packed);
 };
 
 // kinetic-energy spectrum (kbc_spectrum.cu): work bytes for an n^3 velocity field in FP64 or

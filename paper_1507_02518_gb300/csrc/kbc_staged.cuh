@@ -184,18 +184,18 @@ __global__ void __launch_bounds__(kSeg, StagedCfg<S>::min_blocks) staged_step_ke
       int guarded, fp64 = 0;
       const uint32_t x = x0 + tid;
       R gamma = collide_step<R, false, false, false, C::rel>(
-          d, cp, &guarded, std::is_same<R, float>::value ? &fp64 : nullptr);
+          d, cp, &guarded, std::is_same<S, float>::value ? &fp64 : nullptr);
       Nbr nb;
       nb.init(g, x, y, z);
-      if (!fp64) {
+      if (MODE == MODE_PULL || !fp64) {  // a flagged node is left to the FP64 pass (AA: not
+                                         // stored)
         Unroll<0, 27>::run([&](auto ic) {
           constexpr int I = decltype(ic)::value;
           S* p = dst + (uint64_t)Pat::store_plane(I) * g.P + nb.template at<I, Pat::store_shift>();
           C::template store_raw<I>(p, d[I]);
         });
-      } else {  // <dh|dh> under kDenFp64: FP64 collision of this node from global memory
-        gamma = (R)fp64_node_update<S, MODE, false, false>(src, dst, g, x, y, z, cp, &guarded);
       }
+      if (fp64) flag_fp64(g, nb.ox[1] + nb.oy[1] + nb.oz[1]);
       if constexpr (RECORD) {
         gamma_out[nb.ox[1] + nb.oy[1] + nb.oz[1]] = (float)gamma;
         if (guarded) atomicAdd(&ctr->guarded, 1ull);

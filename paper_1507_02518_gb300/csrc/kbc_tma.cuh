@@ -210,13 +210,16 @@ __global__ void __launch_bounds__(kRowsThreads, 3)
     if (!active) continue;
 
     int guarded, fp64 = 0;
-    float2 gamma = collide_step<float2, false, false, false, C::rel>(d, cp, &guarded, &fp64);
+    float2 gamma = collide_step<float2, false, false, false, C::rel>(
+        d, cp, &guarded, std::is_same<S, float>::value ? &fp64 : nullptr);
 
-    // stores where f(t+1) expects them (Pattern<MODE>)
+    // stores where f(t+1) expects them (Pattern<MODE>); flagged lanes are left to the FP64
+    // pass (pull: stored anyway, the pass overwrites them from src; AA: not stored)
     const uint64_t n = (uint64_t)x + (uint64_t)g.nx * (y + (uint64_t)g.ny * z);
+    const int skip = MODE == MODE_PULL ? 0 : fp64;
     if constexpr (MODE != MODE_AA_ODD) {
       S* p = dst + n;
-      if (!fp64) {
+      if (!skip) {
         Unroll<0, 27>::run([&](auto ic) {
           constexpr int I = decltype(ic)::value;
           LD::put2(p + (uint64_t)Pat::store_plane(I) * g.P, d[I]);
@@ -225,8 +228,8 @@ __global__ void __launch_bounds__(kRowsThreads, 3)
         Unroll<0, 27>::run([&](auto ic) {
           constexpr int I = decltype(ic)::value;
           S* q = p + (uint64_t)Pat::store_plane(I) * g.P;
-          if (!(fp64 & 1)) LD::put1(q, d[I].x);
-          if (!(fp64 & 2)) LD::put1(q + 1, d[I].y);
+          if (!(skip & 1)) LD::put1(q, d[I].x);
+          if (!(skip & 2)) LD::put1(q + 1, d[I].y);
         });
       }
     } else {
@@ -237,12 +240,12 @@ __global__ void __launch_bounds__(kRowsThreads, 3)
                               (y + 1 == g.ny ? 0 : y + 1) * g.nx};
       const uint32_t oz[3] = {(z == 0 ? g.nz - 1 : z - 1) * g.nxy, z * g.nxy,
                               (z + 1 == g.nz ? 0 : z + 1) * g.nxy};
-      const bool wa = !(fp64 & 1), wb = !(fp64 & 2);
+      const bool wa = !(skip & 1), wb = !(skip & 2);
       Unroll<0, 27>::run([&](auto ic) {
         constexpr int I = decltype(ic)::value;
         S* rowp = dst + (uint64_t)I * g.P + oy[cy(I) + 1] + oz[cz(I) + 1];
         if constexpr (cx(I) == 0) {
-          if (!fp64) {
+          if (!skip) {
             LD::put2(rowp + x, d[I]);
           } else {
             if (wa) LD::put1(rowp + x, d[I].x);
@@ -257,16 +260,9 @@ __global__ void __launch_bounds__(kRowsThreads, 3)
         }
       });
     }
-    if (fp64) {  // lanes whose <dh|dh> fell under kDenFp64: FP64 collision of those nodes
-      int g64 = 0;
-      if (fp64 & 1) {
-        gamma.x = fp64_node_update<S, MODE, false, false>(src, dst, g, x, y, z, cp, &g64);
-        guarded = (guarded & ~1) | g64;
-      }
-      if (fp64 & 2) {
-        gamma.y = fp64_node_update<S, MODE, false, false>(src, dst, g, x + 1, y, z, cp, &g64);
-        guarded = (guarded & ~2) | (g64 << 1);
-      }
+    if (fp64) {
+      if (fp64 & 1) flag_fp64(g, (uint32_t)n);
+      if (fp64 & 2) flag_fp64(g, (uint32_t)n + 1);
     }
     if constexpr (RECORD) {
       *reinterpret_cast<float2*>(gamma_out + n) = gamma;

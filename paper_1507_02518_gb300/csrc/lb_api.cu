@@ -56,6 +56,8 @@ template <typename F> lb_status no_throw(F&& f) {
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 size_t elem_size(int storage) { return storage == LB_F64 ? 8 : (storage == LB_F32 ? 4 : 2); }
+// the FP64 re-collision mask of P nodes: one bit per node, whole 32-bit words
+size_t fbmask_bytes(uint64_t P) { return (size_t)((P + 31) / 32) * 4; }
 size_t arith_size(int storage) { return storage == LB_F64 ? 8 : 4; }
 
 bool valid_config(const lb_config* c, std::string* why) {
@@ -101,9 +103,10 @@ bool valid_config(const lb_config* c, std::string* why) {
   return true;
 }
 
-// per-box region: populations (1 or 2 arrays), gamma field, step counters
+// per-box region: populations (1 or 2 arrays), gamma field, step counters, the mask of nodes
+// flagged for the FP64 re-collision (one bit per node)
 struct BoxLayout {
-  size_t pop0, pop1, gamma, counters, total;
+  size_t pop0, pop1, gamma, counters, fbmask, total;
 };
 BoxLayout box_layout(const lb_config* c, size_t off) {
   const uint64_t P = (uint64_t)c->nx * c->ny * c->nz;
@@ -120,6 +123,8 @@ BoxLayout box_layout(const lb_config* c, size_t off) {
   off += P * sizeof(float);
   L.counters = off = align_up(off);
   off += sizeof(kbc::StepCounters);
+  L.fbmask = off = align_up(off);
+  off += fbmask_bytes(P);
   L.total = align_up(off);
   return L;
 }
@@ -321,6 +326,7 @@ void setup_ctx(lb_ctx* c, const lb_config* cfg, char* base, const BoxLayout& B,
   c->n_first = 0;
   c->n_count = c->box.P;
   c->counters = (kbc::StepCounters*)(base + B.counters);
+  c->box.fbmask = (uint32_t*)(base + B.fbmask);
   c->stream = st;
   c->ufield = base + S.ufield;
   c->partials = (double*)(base + S.partials);
@@ -345,6 +351,7 @@ lb_status zero_state(lb_ctx* c) {
   if (e == cudaSuccess && c->box.pop[1] != c->box.pop[0])
     e = cudaMemsetAsync(c->box.pop[1], 0, bytes, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->counters, 0, sizeof(kbc::StepCounters), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->box.fbmask, 0, fbmask_bytes(c->box.P), c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "clearing populations");
   c->t = 0;
   c->gamma_valid = false;
@@ -1184,11 +1191,14 @@ struct lb_batch {
   std::vector<lb_config> cfgs;
   kbc::BoxDesc* d_boxes = nullptr;
   kbc::WorkItem* d_items = nullptr;
+  kbc::BatchFlags* d_flags = nullptr;  // the batch-wide flag of the FP64 re-collision pass
   size_t max_items = 0;
   int nitems = 0;
   int threads = 256;
   int tile = 512;  // target nodes per work item
-  bool packed = false;  // FP32x2 two-nodes-per-thread kernel (FP32 arithmetic only)
+  // 0 one node per thread; FP32 arithmetic only: 1 FP32x2 pairs (n, n + 32), 2 FP32x2 adjacent
+  // pairs (x, x + 1) (every box with an even nx, natural moments)
+  int packed = 0;
   int grid = 1;
   cudaStream_t stream = nullptr;
   cudaStream_t capture_stream = nullptr;
@@ -1204,8 +1214,19 @@ lb_status bfail(lb_batch* b, lb_status s, const std::string& m) {
   return s;
 }
 
+// The batch kernel a kernel request selects: 0 one node per thread (FP64 arithmetic, or
+// LB_KERNEL_DIRECT), 1 the FP32x2 (n, n + 32) pairs, 2 the FP32x2 adjacent pairs, which AUTO
+// takes whenever every box has an even nx and the moments are natural (as for one box).
+int batch_kind(const lb_config* cfgs, int nbox, int32_t kind) {
+  if (cfgs[0].storage == LB_F64 || kind == LB_KERNEL_DIRECT) return 0;
+  if (kind == LB_KERNEL_PACKED) return 1;
+  bool even = cfgs[0].variant < LB_S_CD;
+  for (int k = 0; k < nbox && even; ++k) even = cfgs[k].nx % 2 == 0;
+  return even ? 2 : 1;
+}
+
 struct BatchLayout {
-  size_t boxes, items, shared_off, total;
+  size_t boxes, items, flags, shared_off, total;
   size_t max_items;
   std::vector<BoxLayout> box;
   SharedLayout shared;
@@ -1239,6 +1260,8 @@ bool batch_layout(const lb_config* cfgs, int32_t nbox, BatchLayout* L, std::stri
   L->items = off;
   L->max_items = rows;
   off = align_up(off + sizeof(kbc::WorkItem) * rows);
+  L->flags = off;
+  off = align_up(off + sizeof(kbc::BatchFlags));
   L->box.clear();
   for (int b = 0; b < nbox; ++b) {
     lb_config c = cfgs[b];
@@ -1315,15 +1338,18 @@ cudaError_t enqueue_batch_step(lb_batch* b, int64_t t, bool record, cudaStream_t
   const int central = c.variant >= LB_S_CD;
   switch (c.storage) {
     case LB_F64:
-      return kbc::Ops<double>::batch_step(b->d_boxes, b->d_items, b->nitems, t, record, false,
+      return kbc::Ops<double>::batch_step(b->d_boxes, b->nbox, b->d_flags, b->d_items,
+                                          b->nitems, t, record, 0,
                                           c.scheme, wt, wq, central, c.gamma_mode, b->threads,
                                           b->grid, st);
     case LB_F32:
-      return kbc::Ops<float>::batch_step(b->d_boxes, b->d_items, b->nitems, t, record,
+      return kbc::Ops<float>::batch_step(b->d_boxes, b->nbox, b->d_flags, b->d_items,
+                                         b->nitems, t, record,
                                          b->packed, c.scheme, wt, wq, central, c.gamma_mode,
                                          b->threads, b->grid, st);
     default:
-      return kbc::Ops<uint16_t>::batch_step(b->d_boxes, b->d_items, b->nitems, t, record,
+      return kbc::Ops<uint16_t>::batch_step(b->d_boxes, b->nbox, b->d_flags, b->d_items,
+                                            b->nitems, t, record,
                                             b->packed, c.scheme, wt, wq, central, c.gamma_mode,
                                             b->threads, b->grid, st);
   }
@@ -1434,8 +1460,9 @@ lb_status lb_batch_create(const lb_config* cfgs, int32_t nbox, void* dev_buf, si
     b->stream = (cudaStream_t)stream;
     b->d_boxes = (kbc::BoxDesc*)(base + L.boxes);
     b->d_items = (kbc::WorkItem*)(base + L.items);
+    b->d_flags = (kbc::BatchFlags*)(base + L.flags);
     b->max_items = L.max_items;
-    b->packed = cfgs[0].storage != LB_F64;
+    b->packed = batch_kind(cfgs, nbox, LB_KERNEL_AUTO);
     if (b->packed) b->threads = 128;
     cudaError_t e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
@@ -1470,6 +1497,7 @@ lb_status lb_batch_create(const lb_config* cfgs, int32_t nbox, void* dev_buf, si
       d.pop[0] = v->box.pop[0];
       d.pop[1] = v->box.pop[1];
       d.gamma = v->box.gamma;
+      d.fbmask = v->box.fbmask;
       d.ctr = v->counters;
       d.beta = v->box.beta;
       d.two_beta = 2.0 * v->box.beta;
@@ -1477,6 +1505,7 @@ lb_status lb_batch_create(const lb_config* cfgs, int32_t nbox, void* dev_buf, si
     }
     e = cudaMemcpyAsync(b->d_boxes, descs.data(), sizeof(kbc::BoxDesc) * nbox,
                         cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_flags, 0, sizeof(kbc::BatchFlags), b->stream);
     if (e != cudaSuccess) {
       g_create_error = "uploading box descriptors: " + std::string(cudaGetErrorString(e));
       return LB_ERR_CUDA;
@@ -1568,12 +1597,18 @@ lb_status lb_batch_diagnostics(lb_batch* b, lb_diag* out) {
 lb_status lb_batch_set_kernel(lb_batch* b, int32_t kind) {
   return no_throw([&]() -> lb_status {
     if (!b) return LB_ERR_INVALID_ARG;
-    if (kind != LB_KERNEL_AUTO && kind != LB_KERNEL_DIRECT && kind != LB_KERNEL_PACKED)
-      return bfail(b, LB_ERR_INVALID_ARG, "batch kernel must be LB_KERNEL_AUTO, _DIRECT or _PACKED");
+    if (kind != LB_KERNEL_AUTO && kind != LB_KERNEL_DIRECT && kind != LB_KERNEL_PACKED &&
+        kind != LB_KERNEL_ADJ)
+      return bfail(b, LB_ERR_INVALID_ARG,
+                   "batch kernel must be LB_KERNEL_AUTO, _DIRECT, _PACKED or _ADJ");
     const bool fp32 = b->base_cfg.storage != LB_F64;
-    if (kind == LB_KERNEL_PACKED && !fp32)
-      return bfail(b, LB_ERR_UNSUPPORTED, "the packed kernel needs FP32 arithmetic");
-    b->packed = fp32 && kind != LB_KERNEL_DIRECT;
+    if ((kind == LB_KERNEL_PACKED || kind == LB_KERNEL_ADJ) && !fp32)
+      return bfail(b, LB_ERR_UNSUPPORTED, "the packed kernels need FP32 arithmetic");
+    const int k = batch_kind(b->cfgs.data(), b->nbox, kind);
+    if (kind == LB_KERNEL_ADJ && k != 2)
+      return bfail(b, LB_ERR_UNSUPPORTED,
+                   "the adjacent-pair kernel needs an even nx in every box and natural moments");
+    b->packed = k;
     b->threads = b->packed ? 128 : 256;
     return build_items(b);
   });

@@ -92,10 +92,13 @@ def test_batch96_sampled_parity(kbc):
     import torch
     boxes = workloads.batch_boxes(96)
     batch = lb.Batch(boxes, storage="f32", scheme="pull")
-    batch.autotune(2)
-    for k, b in enumerate(boxes):
-        _, u = workloads.random_spectrum(b["n"], b["k0"], b["urms"], b["seed"])
-        lb.lb_init_field(batch.box(k), 0, np.ascontiguousarray(u).ctypes.data, False)
+    fields = [np.ascontiguousarray(workloads.random_spectrum(b["n"], b["k0"], b["urms"],
+                                                             b["seed"])[1]) for b in boxes]
+    for _ in range(2):          # tuned on the initial fields, which are then set again
+        for k in range(len(boxes)):
+            lb.lb_init_field(batch.box(k), 0, fields[k].ctypes.data, False)
+        if _ == 0:
+            batch.autotune(2)
     torch.cuda.synchronize()
     batch.step(3)
     sizes = [b["n"] for b in boxes]

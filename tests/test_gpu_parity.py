@@ -556,10 +556,16 @@ def test_nonfinite_is_reported(kbc):
 @pytest.mark.parametrize("storage,scheme,kind", [("f32", "pull", "direct"), ("f32", "aa", "direct"),
                                                  ("f64", "pull", "direct"), ("f16", "aa", "direct"),
                                                  ("f32", "pull", "packed"), ("f32", "aa", "packed"),
-                                                 ("f16", "aa", "packed"), ("f16", "pull", "packed")])
+                                                 ("f16", "aa", "packed"), ("f16", "pull", "packed"),
+                                                 ("f32", "pull", "adj"), ("f32", "aa", "adj"),
+                                                 ("f16", "aa", "adj"), ("f16", "pull", "adj")])
 def test_batch_matches_single_boxes_bitwise(kbc, storage, scheme, kind):
-    boxes = [{"n": 12, "nu": 1e-3}, {"n": 9, "ny": 14, "nz": 5, "nu": 3e-4},
-             {"n": 33, "ny": 4, "nz": 6, "nu": 2e-5}]
+    if kind == "adj":   # every nx even; rows of 4, 10, 12 and 34 nodes (items cross rows)
+        boxes = [{"n": 12, "nu": 1e-3}, {"n": 10, "ny": 14, "nz": 5, "nu": 3e-4},
+                 {"n": 34, "ny": 4, "nz": 6, "nu": 2e-5}, {"n": 4, "ny": 6, "nz": 3, "nu": 1e-3}]
+    else:
+        boxes = [{"n": 12, "nu": 1e-3}, {"n": 9, "ny": 14, "nz": 5, "nu": 3e-4},
+                 {"n": 33, "ny": 4, "nz": 6, "nu": 2e-5}]
     batch = lb.Batch(boxes, storage=storage, scheme=scheme)
     batch.set_kernel(kind)
     states = []
@@ -583,7 +589,73 @@ def test_batch_matches_single_boxes_bitwise(kbc, storage, scheme, kind):
         lb.lb_get_populations(batch.box(k), got.ctypes.data, False)
         assert np.array_equal(got, single.get_populations()), k
     diags = batch.diagnostics()
-    assert len(diags) == 3 and all(d["step"] == 7 for d in diags)
+    assert len(diags) == len(boxes) and all(d["step"] == 7 for d in diags)
+
+
+@pytest.mark.parametrize("scheme", ["pull", "aa"])
+@pytest.mark.parametrize("kind", ["direct", "packed", "adj"])
+def test_batch_fp64_pass_matches_single_boxes(kbc, scheme, kind):
+    """Boxes 0 and 2 start 1e-7 (relative) from equilibrium, so every node of theirs goes to
+    the FP64 re-collision pass; box 1 starts 1e-3 away, so none of its nodes does. Each box of
+    the batch ends with the single-box populations and gammas, bit for bit."""
+    boxes = [{"n": 12, "nu": 1e-3}, {"n": 10, "nu": 3e-4}, {"n": 14, "nu": 2e-4}]
+    noises = [1e-7, 1e-3, 1e-7]
+    batch = lb.Batch(boxes, storage="f32", scheme=scheme)
+    batch.set_kernel(kind)
+    states = []
+    for k, (b, noise) in enumerate(zip(boxes, noises)):
+        n = b["n"]
+        rho, u = workloads.random_spectrum(n, 3, 0.04, seed=60 + k)
+        f0 = oracle.init_equilibrium(rho, u) * (
+            1 + noise * workloads.population_noise(n, n, n, 61 + k))
+        states.append(np.ascontiguousarray(f0))
+        lb.lb_set_populations(batch.box(k), states[-1].ctypes.data, False)
+    batch.step(3)
+    for k, b in enumerate(boxes):
+        n = b["n"]
+        single = lb.Lattice(n, nu=b["nu"], storage="f32", scheme=scheme)
+        single.set_kernel(kind)
+        single.set_populations(states[k])
+        single.step(3)
+        got = np.empty((27, n, n, n))
+        lb.lb_get_populations(batch.box(k), got.ctypes.data, False)
+        assert np.array_equal(got, single.get_populations()), k
+        g = np.empty((n, n, n), dtype=np.float32)
+        lb.lb_get_gamma(batch.box(k), g.ctypes.data, False)
+        assert np.array_equal(g, single.gamma()), k
+        single.close()
+
+
+def test_rest_state_steps_through_the_fp64_pass(kbc):
+    """At rest every FP32 node has <dh|dh> = 0 and is re-collided in FP64 each step; the
+    populations stay at rest to FP32 rounding, and the pass leaves nothing flagged behind
+    (the next steps from a disturbed state equal a fresh box's)."""
+    n = 16
+    lat = lattice((n, n, n), storage="f32", scheme="aa")
+    lat.step(4)
+    f = lat.get_populations()
+    assert np.max(np.abs(f - W4)) <= 1e-8
+    f0 = seeded_state(n, n, n, seed=70)
+    lat.set_populations(f0)
+    lat.step(3)
+    fresh = lattice((n, n, n), storage="f32", scheme="aa")
+    fresh.set_populations(f0)
+    fresh.step(3)
+    assert np.array_equal(lat.get_populations(), fresh.get_populations())
+    assert np.array_equal(lat.gamma(), fresh.gamma())
+
+
+def test_batch_adj_kernel_needs_even_rows(kbc):
+    batch = lb.Batch([{"n": 12, "nu": 1e-3}, {"n": 9, "nu": 1e-3}], storage="f32", scheme="aa")
+    with pytest.raises(lb.LBError) as e:
+        batch.set_kernel("adj")
+    assert e.value.status == lb.LB_ERR_UNSUPPORTED
+    batch.set_kernel("auto")            # falls back to the (n, n + 32) pairs
+    batch.step(2)
+    f64 = lb.Batch([{"n": 12, "nu": 1e-3}], storage="f64", scheme="aa")
+    with pytest.raises(lb.LBError) as e:
+        f64.set_kernel("adj")
+    assert e.value.status == lb.LB_ERR_UNSUPPORTED
 
 
 def test_batch_autotune_and_graph_replay(kbc):

@@ -7,6 +7,7 @@ default and the row-staged kernels. The neighbour ring is periodic."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_1507_02518_gb300 import lb, slab, workloads
 
 from test_gpu_parity import lattice, seeded_state
@@ -52,6 +53,30 @@ def test_slabs_with_each_fp32_kernel(kbc, storage, scheme, kind):
         s.set_populations(f0[:, s.z0:s.z0 + s.nz_local])
     slab.step_local(slabs, 10)
     assert np.array_equal(gather(slabs), ref.get_populations())
+
+
+@pytest.mark.parametrize("scheme", ["pull", "aa"])
+@pytest.mark.parametrize("kind", ["packed", "adj"])
+def test_slabs_with_nodes_recollided_in_fp64(kbc, scheme, kind):
+    """1e-7 (relative) from equilibrium every FP32 node is re-collided in FP64 by the pass
+    that follows each step kernel, the boundary planes' pass before their faces are packed:
+    populations and gammas equal the single box's bit for bit."""
+    n = 12
+    rho, u = workloads.random_spectrum(n, 3, 0.04, seed=33)
+    f0 = oracle.init_equilibrium(rho, u) * (1 + 1e-7 * workloads.population_noise(n, n, n, 34))
+    ref = lattice((n, n, n), storage="f32", scheme=scheme)
+    ref.set_kernel(kind)
+    ref.set_populations(f0)
+    ref.step(4)
+    slabs = slab.make_slabs(n, n, n, 3, storage="f32", scheme=scheme)
+    for s in slabs:
+        s.set_kernel(kind)
+        s.set_populations(f0[:, s.z0:s.z0 + s.nz_local])
+    slab.step_local(slabs, 3)
+    slab.step_local(slabs, 1, record=True)
+    assert np.array_equal(gather(slabs), ref.get_populations())
+    g = np.concatenate([lb_gamma(s) for s in slabs], axis=0)
+    assert np.array_equal(g, ref.gamma())
 
 
 def test_slab_init_moments_gamma_and_one_plane_slabs(kbc):
