@@ -295,7 +295,10 @@ def run_box(w, steps, warmup, want_kernel_time=True):
     torch.cuda.synchronize()
     total_ms = e_start.elapsed_time(e_end)
     step_ms = sum(a.elapsed_time(b) for a, b in ev)
-    launches = steps + (3 * len(diags))
+    # per step the step kernel, plus the FP64 re-collision pass after it with FP32 storage
+    # (estimate of gamma); per diagnostics call two field kernels and two final sums
+    per_step = 2 if (w["storage"] == "f32" and w.get("gamma", "estimate") == "estimate") else 1
+    launches = steps * per_step + 4 * len(diags)
     out = {"P": lat.P, "steps": steps, "total_ms": total_ms, "step_kernel_ms": step_ms / steps,
            "launches": launches, "diag": diags[-1] if diags else None, "lat": lat}
     return out
@@ -380,7 +383,9 @@ def run_strong(w, steps, warmup, rank, world):
     torch.cuda.synchronize()
     ms = a.elapsed_time(b)
     nz_local = z1 - z0
-    launches = steps * ((2 if nz_local > 1 else 1) + (1 if nz_local > 2 else 0) + 2)
+    per_kernel = 2 if w["storage"] == "f32" else 1   # step kernel (+ FP64 re-collision pass)
+    launches = steps * (per_kernel * ((2 if nz_local > 1 else 1) + (1 if nz_local > 2 else 0))
+                        + 2)
     s.close()
     return {"P": n * n * nz_local, "P_box": n ** 3, "total_ms": ms, "launches": launches,
             "planes": [z0, z1], "face_bytes": 9 * n * n * {"f64": 8, "f32": 4, "f16": 2}[
