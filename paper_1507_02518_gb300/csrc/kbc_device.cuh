@@ -1333,8 +1333,8 @@ __device__ __forceinline__ void node_update_adj(const S* src, S* dst, const Geo&
   oz[0] = (z == 0 ? g.nz - 1 : z - 1) * g.nxy;
   oz[1] = z * g.nxy;
   oz[2] = (z + 1 == g.nz ? 0 : z + 1) * g.nxy;
-  const uint32_t xm = x == 0 ? g.nx - 1 : x - 1;
-  const uint32_t xp2 = x + 2 == g.nx ? 0 : x + 2;
+  uint32_t xm = x == 0 ? g.nx - 1 : x - 1;
+  uint32_t xp2 = x + 2 == g.nx ? 0 : x + 2;
   float2 d[27];
   Unroll<0, 27>::run([&](auto ic) {
     constexpr int I = decltype(ic)::value;
@@ -1355,6 +1355,20 @@ __device__ __forceinline__ void node_update_adj(const S* src, S* dst, const Geo&
   uint64_t Ps = g.P;
   S* dsts = dst;
   if constexpr (MODE != MODE_PULL) asm volatile("" : "+l"(Ps), "+l"(dsts));
+  if constexpr (MODE == MODE_AA_ODD) {
+    // the odd step stores to the neighbours: their row offsets and x positions are rebuilt
+    // from opaque copies of the coordinates rather than kept live across the collision
+    uint32_t x2 = x, y2 = y, z2 = z;
+    asm volatile("" : "+r"(x2), "+r"(y2), "+r"(z2));
+    oy[0] = (y2 == 0 ? g.ny - 1 : y2 - 1) * g.nx;
+    oy[1] = y2 * g.nx;
+    oy[2] = (y2 + 1 == g.ny ? 0 : y2 + 1) * g.nx;
+    oz[0] = (z2 == 0 ? g.nz - 1 : z2 - 1) * g.nxy;
+    oz[1] = z2 * g.nxy;
+    oz[2] = (z2 + 1 == g.nz ? 0 : z2 + 1) * g.nxy;
+    xm = x2 == 0 ? g.nx - 1 : x2 - 1;
+    xp2 = x2 + 2 == g.nx ? 0 : x2 + 2;
+  }
   Unroll<0, 27>::run([&](auto ic) {
     constexpr int I = decltype(ic)::value;
     constexpr int SS = Pat::store_shift;
