@@ -57,6 +57,24 @@ def test_required_bytes_and_validation(lib):
     assert lb.lb_required_bytes(c_bad) == 0
 
 
+def test_slab_and_mask_sizes_on_host(lib):
+    """A slab context holds its planes plus one halo plane per side, the FP64 re-collision mask
+    (one bit per node), and four face buffers of 9 nx ny stored values; invalid slabs size to 0."""
+    from paper_1507_02518_gb300 import lb
+    nx, ny, nz = 24, 16, 12
+    g = lb.make_config(nx, ny, nz, storage="f32", scheme="aa")
+    for k in (1, 3, nz):
+        need = lb.lb_slab_required_bytes(g, k)
+        box = lb.lb_required_bytes(lb.make_config(nx, ny, k + 2, storage="f32", scheme="aa"))
+        assert need >= box + 4 * 9 * nx * ny * 4
+        assert need >= 27 * nx * ny * (k + 2) * 4 + (nx * ny * (k + 2) + 31) // 32 * 4
+    for bad in (0, -1, nz + 1):
+        assert lb.lb_slab_required_bytes(g, bad) == 0
+    # the mask grows with the node count: one bit per node on top of the populations
+    small = lb.lb_required_bytes(lb.make_config(32, storage="f16", scheme="aa"))
+    assert small >= 27 * 32 ** 3 * 2 + 32 ** 3 // 8 + 32 ** 3 * 4
+
+
 def test_create_rejects_bad_arguments_on_host(lib):
     from paper_1507_02518_gb300 import lb
     with pytest.raises(lb.LBError) as e:
