@@ -801,6 +801,27 @@ def test_max_size_768cubed_fp16_aa_sampled_parity(kbc):
     _sampled_step_check(lat, 24, FP32_STEP_TOL, rng, half=True)     # the even step t = 4 -> 5
 
 
+def test_max_size_768cubed_fp32_aa_sampled_parity(kbc):
+    """The 768^3 decaying-turbulence configuration in FP32 AA (453 M nodes, 49 GB in place):
+    the first step from f_eq sends every node through the FP64 re-collision pass at full size,
+    then one-step parity of the odd and the even step at sampled nodes."""
+    import torch
+    n, nu = 768, 2e-5
+    _, u = workloads.random_spectrum_device(n, 4.0, 0.05, 1, "cuda")
+    lat = lb.Lattice(n, nu=nu, storage="f32", scheme="aa")
+    lat.init_field(None, u)
+    del u
+    torch.cuda.empty_cache()
+    d0 = lat.diagnostics()
+    lat.step(3)
+    d1 = lat.diagnostics()
+    assert d1["nonfinite_count"] == 0
+    assert abs(d1["mass"] - d0["mass"]) / d0["mass"] < 1e-7
+    rng = np.random.default_rng(5)
+    _sampled_step_check(lat, 24, FP32_STEP_TOL, rng)     # the odd step t = 3 -> 4
+    _sampled_step_check(lat, 24, FP32_STEP_TOL, rng)     # the even step t = 4 -> 5
+
+
 def test_run_logs_diagnostics_as_json_lines(kbc, tmp_path):
     import json
     lat = lattice((16, 16, 16), storage="f32", scheme="aa")
