@@ -41,3 +41,31 @@ def test_workload_names_parse():
         bench.parse_workload("hit64_bf16_pull")
     a = bench.parse_args(["--variants", "batch16_f32_pull,hit64_f32_aa"])
     assert a.variants == "batch16_f32_pull,hit64_f32_aa" and a.warmup >= 3
+
+
+def test_roofline_arithmetic_and_the_kernel_hash(tmp_path, monkeypatch):
+    """achieved = algorithmic bytes per update x updates per second; frac = achieved / peak;
+    the hash that keys the ncu traffic figure moves with the kernel sources, the kernel
+    selection and the launch code alike."""
+    import shutil
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench.roofline("f32", 30000.0, 6789.6, "measured", traffic=3.58e9)
+    assert r["achieved"] == round(216 * 30000e6 / 1e9, 1)
+    assert abs(r["frac"] - r["achieved"] / 6789.6) < 1e-4
+    assert r["traffic"] == 3.58e9 and r["peak_source"] == "of measured" and r["bound"] == "hbm"
+    assert bench.roofline("f16", 1000.0, 1000.0, "fallback")["achieved"] == 108.0
+    assert {"kbc_device.cuh", "kbc_kernels.cuh", "kbc_ops.h", "lb_api.cu"} <= set(
+        bench.KERNEL_SOURCES)
+    src = os.path.join(ROOT, "paper_1507_02518_gb300", "csrc")
+    dst = tmp_path / "paper_1507_02518_gb300" / "csrc"
+    shutil.copytree(src, dst)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.kernel_source_hash()
+    assert h0 == bench.kernel_source_hash()
+    for name in ("lb_api.cu", "kbc_ops.h", "kbc_device.cuh"):
+        with open(dst / name, "a") as fh:
+            fh.write("\n")
+        h1 = bench.kernel_source_hash()
+        assert h1 != h0, name
+        h0 = h1
